@@ -1,0 +1,28 @@
+"""Plain CPU FP64 oracle for the partitioned poro-elastic + cohesive-fault solver.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import anything from here.
+The GPU library never calls it and shares no code with it.
+
+It restates, with assembled sparse matrices and library linear algebra, what the
+paper (Gallyamov et al., "A Parallelized 3D Geomechanical Solver for
+Fluid-induced Fault Slip in Poroelastic Media") defines:
+
+  fem.py       Q1 element matrices (Sec. 3.2, App. A), fault geometry, the
+               double-node fracture-flow operators (Sec. 3.1.2, 3.2.3, App. B)
+               and global assembly.
+  law.py       contact / Coulomb return map (Sec. 2.2.1, Eqs. normal_traction,
+               yield_function, slip_split, plastic_slip_increment, corrector).
+  solve.py     Newton on the incremental residuals (Sec. 3.3.1, Eqs.
+               nonlinear_system, linear_system), dense LU, sparse direct and
+               Prevost's partitioned CG (Sec. 3.3.2, Eqs. prevost_system,
+               schur_system).
+  analytic.py  closed forms used to pin the oracle: 1-D consolidation series,
+               the line-source (Theis) fault pressure, the circular slip-front
+               amplification lambda(T) (Sec. 4.2).
+  rows.py      the same operators evaluated one node at a time, for sampled
+               checks on meshes too large to assemble.
+
+Parity status per function is stated in each docstring ("pinned by ..." or
+"parity unpinned").
+"""

@@ -1,0 +1,343 @@
+"""Seeded synthetic inputs shared by the oracle and the GPU library.
+
+This module only *describes* problems: grid sizes, material values, fault
+parameters, boundary masks, nodal loads, time-step schedules and seeded random
+fields.  It contains none of the method's arithmetic (no element matrices, no
+fault law, no solver), so that the CPU oracle and the CUDA path can both start
+from the same numbers while sharing no computation.
+
+Node numbering (used by both sides, and by the C-ABI):
+  a structured grid of nx x ny x nz hexahedra.  Node planes are counted along z.
+  When a fault plane at original node plane ``kf`` is present, that plane is
+  duplicated: extended plane ``kf`` is the lower lip ("-" side) and extended
+  plane ``kf + 1`` is the upper lip ("+" side), so there are nz + 2 planes.
+  node id n = i + (nx + 1) * (j + (ny + 1) * kk),  kk in [0, n_planes).
+  Element (ei, ej, ek) uses extended planes kb, kb + 1 with
+  kb = ek + (1 if fault and ek >= kf else 0).
+  Element id e = ei + nx * (ej + ny * ek).
+Vectors are stored field-major ("SoA"): u as (3, N), p as (N,).
+
+The workloads restate the paper's verification and application set-ups
+(Sec. 4.2 injection-induced slip, Table 1; Sec. 5 faulted aquifer) on
+structured grids; the paper's own meshes and datasets are not used.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+__all__ = [
+    "FaultParams",
+    "Problem",
+    "node_id",
+    "n_planes",
+    "fault_small",
+    "slip_front",
+    "inclined_lognormal",
+    "column_terzaghi",
+    "theis_plate",
+    "tiny_faulted",
+    "random_vectors",
+    "random_displacement_jump",
+    "CONFIGS",
+]
+
+
+@dataclasses.dataclass
+class FaultParams:
+    """Cohesive-fault and fracture-flow parameters (Sec. 2.2, Table 1).
+
+    kn, ks   normal / shear penalty stiffness [Pa/m]
+    f        Coulomb friction coefficient [-]
+    w0       hydraulic aperture used by the fault flow operators [m]
+    wk_par   longitudinal transmissibility w * k_par [m^3]
+    k_perp   transverse permeability [m^2]; <= 0 means infinite (tied p+ = p-)
+    MF       fracture Biot modulus [Pa]
+    tn0      in-situ effective normal traction, compression positive [Pa]
+    tau0     in-situ shear traction in the fault frame (t1, t2) [Pa]
+    """
+
+    kn: float
+    ks: float
+    f: float
+    w0: float
+    wk_par: float
+    k_perp: float
+    MF: float
+    tn0: float
+    tau0: tuple
+
+    def as_tuple(self):
+        return (self.kn, self.ks, self.f, self.w0, self.wk_par, self.k_perp,
+                self.MF, self.tn0, float(self.tau0[0]), float(self.tau0[1]))
+
+
+@dataclasses.dataclass
+class Problem:
+    """One synthetic problem: grid, materials, fault, constraints, loads, steps."""
+
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    origin: tuple
+    h: tuple
+    shear: tuple            # (dz/dx, dz/dy) of the affine map
+    kf: Optional[int]       # original node-plane index of the fault, or None
+    fault: Optional[FaultParams]
+    E: np.ndarray           # Young's modulus per element [Pa]
+    k: np.ndarray           # permeability per element [m^2]
+    nu: float
+    alpha: float
+    M: float                # Biot modulus [Pa]
+    mu_f: float             # fluid viscosity [Pa s]
+    fixed: np.ndarray       # uint8 (4, N): 1 = homogeneous Dirichlet on (ux,uy,uz,p)
+    fu: np.ndarray          # (3, N) nodal forces [N]
+    fp: np.ndarray          # (N,) nodal fluid sources [m^3/s]
+    dts: list               # time-step sizes [s]
+    notes: str = ""
+
+    @property
+    def n_planes(self) -> int:
+        return n_planes(self.nz, self.kf)
+
+    @property
+    def n_nodes(self) -> int:
+        return (self.nx + 1) * (self.ny + 1) * self.n_planes
+
+    @property
+    def n_el(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def n_pairs(self) -> int:
+        return 0 if self.kf is None else (self.nx + 1) * (self.ny + 1)
+
+    @property
+    def n_dof(self) -> int:
+        return 4 * self.n_nodes
+
+
+def n_planes(nz: int, kf: Optional[int]) -> int:
+    return nz + 1 + (0 if kf is None else 1)
+
+
+def node_id(nx: int, ny: int, i, j, kk):
+    return np.asarray(i) + (nx + 1) * (np.asarray(j) + (ny + 1) * np.asarray(kk))
+
+
+def _empty(nx, ny, nz, kf):
+    N = (nx + 1) * (ny + 1) * n_planes(nz, kf)
+    return (np.zeros((4, N), np.uint8), np.zeros((3, N)), np.zeros(N))
+
+
+def _fix_bottom(fixed, nx, ny):
+    """u = 0 on the bottom face (extended plane 0)."""
+    nb = (nx + 1) * (ny + 1)
+    fixed[0:3, :nb] = 1
+
+
+def _inject_centre(fp, nx, ny, kf, Q):
+    """Constant-rate injection at the centre fault pair, split half/half
+    between the two lips (Sec. 4.2)."""
+    ic, jc = nx // 2, ny // 2
+    fp[node_id(nx, ny, ic, jc, kf)] += 0.5 * Q
+    fp[node_id(nx, ny, ic, jc, kf + 1)] += 0.5 * Q
+
+
+# ---------------------------------------------------------------------------
+# Workload definitions
+# ---------------------------------------------------------------------------
+
+def fault_small(n: int = 8, Q: float = 5e-5, steps: int = 5, dt: float = 2.0) -> Problem:
+    """Unit cube, n^3 Q1 hexes, horizontal fault at mid-height, centre injection.
+
+    E=20 GPa, nu=0.25, alpha=0.8, M=50 GPa, k=1e-15 m^2, mu=1e-3 Pa s;
+    fault f=0.6, in-situ sigma'_n0=10 MPa, tau0=5.4 MPa along x, Table-1
+    fracture-flow values, tied lip pressures; 5 steps of 2 s.  Penalties
+    follow Table 1's kn/E and ks/E ratios per metre: kn=2e12, ks=2e11 Pa/m.
+    """
+    nx = ny = nz = n
+    kf = n // 2
+    fixed, fu, fp = _empty(nx, ny, nz, kf)
+    _fix_bottom(fixed, nx, ny)
+    _inject_centre(fp, nx, ny, kf, Q)
+    nel = nx * ny * nz
+    fault = FaultParams(kn=2e12, ks=2e11, f=0.6, w0=1e-4, wk_par=1e-15, k_perp=0.0,
+                        MF=0.2e6, tn0=10e6, tau0=(5.4e6, 0.0))
+    return Problem(name=f"fault{n}", nx=nx, ny=ny, nz=nz, origin=(0.0, 0.0, 0.0),
+                   h=(1.0 / n,) * 3, shear=(0.0, 0.0), kf=kf, fault=fault,
+                   E=np.full(nel, 20e9), k=np.full(nel, 1e-15), nu=0.25, alpha=0.8,
+                   M=50e9, mu_f=1e-3, fixed=fixed, fu=fu, fp=fp, dts=[dt] * steps,
+                   notes="unit cube, mid-height fault, centre injection")
+
+
+def slip_front(n: int = 64, steps: int = 50, ratio: float = 0.99, T: float = 0.1,
+               dt0: float = 1.0, growth: float = 1.115) -> Problem:
+    """Sec. 4.2 restated on a structured grid: 40 m cube, n^3 hexes, fault at z=0.
+
+    Table 1 values (E=60 GPa, nu=0, k_M=0, alpha=0, M=1e5 GPa, mu=0.89 mPa s,
+    f=0.6, kn=6e3 GPa/m, ks=6e2 GPa/m, wk_par=1e-15 m^3, k_perp infinite,
+    M_F=0.2 MPa), sigma'_0 = 80 MPa.  tau0 = ratio * f * sigma'_0 and the
+    injection rate Q is chosen so that the stress-injection parameter equals T,
+    i.e. Q = 4 pi wk_par dp* / mu with dp* = (1 - ratio) sigma'_0 / T.
+    Geometric time steps dt_k = dt0 * growth^k.
+    """
+    nx = ny = nz = n
+    kf = n // 2
+    L = 40.0
+    fixed, fu, fp = _empty(nx, ny, nz, kf)
+    _fix_bottom(fixed, nx, ny)
+    mu = 0.89e-3
+    wk = 1e-15
+    sig0 = 80e6
+    dpstar = (1.0 - ratio) * sig0 / T
+    Q = 4.0 * math.pi * wk * dpstar / mu
+    _inject_centre(fp, nx, ny, kf, Q)
+    nel = nx * ny * nz
+    fault = FaultParams(kn=6e12, ks=6e11, f=0.6, w0=1e-4, wk_par=wk, k_perp=0.0,
+                        MF=0.2e6, tn0=sig0, tau0=(ratio * 0.6 * sig0, 0.0))
+    dts = [dt0 * growth ** s for s in range(steps)]
+    return Problem(name=f"slipfront{n}", nx=nx, ny=ny, nz=nz,
+                   origin=(-L / 2, -L / 2, -L / 2), h=(L / n,) * 3, shear=(0.0, 0.0),
+                   kf=kf, fault=fault, E=np.full(nel, 60e9), k=np.zeros(nel),
+                   nu=0.0, alpha=0.0, M=1e14, mu_f=mu, fixed=fixed, fu=fu, fp=fp,
+                   dts=dts, notes=f"ratio={ratio} T={T} Q={Q:.6e}")
+
+
+def inclined_lognormal(n: int = 160, steps: int = 20, seed: int = 3,
+                       dip_deg: float = 60.0, dt: float = 5.0, Q: float = 2e-4) -> Problem:
+    """n^3 hexes on a sheared grid whose fault node plane dips ``dip_deg``.
+
+    Per-element log10 k ~ N(-15, 0.5) and E ~ U[10, 30] GPa from
+    numpy default_rng(seed); nu=0.25, alpha=0.8, M=50 GPa; fault f=0.6,
+    sigma'_n0=10 MPa, tau0=5.4 MPa along the dip direction, tied lip pressures.
+    The grid spacing is 1 m; the affine map adds dz = tan(dip) * x.
+    """
+    nx = ny = nz = n
+    kf = n // 2
+    fixed, fu, fp = _empty(nx, ny, nz, kf)
+    _fix_bottom(fixed, nx, ny)
+    _inject_centre(fp, nx, ny, kf, Q)
+    rng = np.random.default_rng(seed)
+    nel = nx * ny * nz
+    logk = rng.normal(-15.0, 0.5, nel)
+    E = rng.uniform(10e9, 30e9, nel)
+    fault = FaultParams(kn=2e12, ks=2e11, f=0.6, w0=1e-4, wk_par=1e-15, k_perp=0.0,
+                        MF=0.2e6, tn0=10e6, tau0=(5.4e6, 0.0))
+    return Problem(name=f"inclined{n}", nx=nx, ny=ny, nz=nz, origin=(0.0, 0.0, 0.0),
+                   h=(1.0, 1.0, 1.0), shear=(math.tan(math.radians(dip_deg)), 0.0),
+                   kf=kf, fault=fault, E=E, k=10.0 ** logk, nu=0.25, alpha=0.8,
+                   M=50e9, mu_f=1e-3, fixed=fixed, fu=fu, fp=fp, dts=[dt] * steps,
+                   notes=f"seed={seed} dip={dip_deg}")
+
+
+def column_terzaghi(nz: int = 16, H: float = 1.0, load: float = 1e6, steps: int = 200,
+                    dt: float = None, E: float = 20e9, nu: float = 0.25,
+                    alpha: float = 0.8, M: float = 50e9, k: float = 1e-15,
+                    mu: float = 1e-3) -> Problem:
+    """One-dimensional consolidation column: 1 x 1 x nz hexes of height H.
+
+    Lateral displacements fixed everywhere (uniaxial strain), u_z = 0 at the
+    bottom, a compressive traction ``load`` on the top face applied from the
+    first step, the top face drained (p = 0), all other faces no-flow.
+    """
+    nx = ny = 1
+    fixed, fu, fp = _empty(nx, ny, nz, None)
+    fixed[0:2, :] = 1
+    nb = (nx + 1) * (ny + 1)
+    fixed[2, :nb] = 1
+    top = slice(nz * nb, (nz + 1) * nb)
+    fixed[3, top] = 1
+    hx = H / nz
+    # consistent nodal forces of a uniform traction on one bilinear face: area/4 each
+    fu[2, top] = -load * (hx * hx) / 4.0
+    nel = nz
+    if dt is None:
+        dt = 1.0
+    return Problem(name=f"terzaghi{nz}", nx=1, ny=1, nz=nz, origin=(0.0, 0.0, 0.0),
+                   h=(hx, hx, hx), shear=(0.0, 0.0), kf=None, fault=None,
+                   E=np.full(nel, E), k=np.full(nel, k), nu=nu, alpha=alpha, M=M,
+                   mu_f=mu, fixed=fixed, fu=fu, fp=fp, dts=[dt] * steps,
+                   notes="1-D consolidation column")
+
+
+def theis_plate(n: int = 32, nz: int = 2, L: float = 40.0, Q: float = 1e-6,
+                steps: int = 30, dt0: float = 0.5, growth: float = 1.15,
+                tn0: float = 80e6) -> Problem:
+    """Fault-plane flow with an impermeable, uncoupled matrix (k_M=0, alpha=0):
+    the fault pressure follows the line-source (Theis) solution (Sec. 4.2).
+    Table-1 fault values, shear far below the friction limit (no slip)."""
+    nx = ny = n
+    kf = nz // 2
+    fixed, fu, fp = _empty(nx, ny, nz, kf)
+    _fix_bottom(fixed, nx, ny)
+    _inject_centre(fp, nx, ny, kf, Q)
+    nel = nx * ny * nz
+    fault = FaultParams(kn=6e12, ks=6e11, f=0.6, w0=1e-4, wk_par=1e-15, k_perp=0.0,
+                        MF=0.2e6, tn0=tn0, tau0=(0.0, 0.0))
+    dts = [dt0 * growth ** s for s in range(steps)]
+    hz = L / n
+    return Problem(name=f"theis{n}", nx=nx, ny=ny, nz=nz, origin=(-L / 2, -L / 2, -hz * kf),
+                   h=(L / n, L / n, hz), shear=(0.0, 0.0), kf=kf, fault=fault,
+                   E=np.full(nel, 60e9), k=np.zeros(nel), nu=0.0, alpha=0.0, M=1e14,
+                   mu_f=0.89e-3, fixed=fixed, fu=fu, fp=fp, dts=dts,
+                   notes="fault-only diffusion")
+
+
+def tiny_faulted(nx: int = 2, ny: int = 2, nz: int = 2, shear=(0.0, 0.0), k_perp: float = 0.0,
+                 seed: Optional[int] = None, Q: float = 2e-5, steps: int = 2,
+                 dt: float = 1.0, h=(0.5, 0.5, 0.5)) -> Problem:
+    """Small faulted box for direct-vs-partitioned and GPU parity checks.
+
+    With ``seed`` the element E and k are drawn from default_rng(seed)
+    (E ~ U[10, 30] GPa, log10 k ~ N(-15, 0.5)); otherwise uniform.
+    """
+    kf = nz // 2
+    fixed, fu, fp = _empty(nx, ny, nz, kf)
+    _fix_bottom(fixed, nx, ny)
+    _inject_centre(fp, nx, ny, kf, Q)
+    nel = nx * ny * nz
+    if seed is None:
+        E = np.full(nel, 20e9)
+        k = np.full(nel, 1e-15)
+    else:
+        rng = np.random.default_rng(seed)
+        E = rng.uniform(10e9, 30e9, nel)
+        k = 10.0 ** rng.normal(-15.0, 0.5, nel)
+    fault = FaultParams(kn=2e12, ks=2e11, f=0.6, w0=1e-4, wk_par=1e-15, k_perp=k_perp,
+                        MF=0.2e6, tn0=10e6, tau0=(5.4e6, 0.0))
+    return Problem(name=f"tiny{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, origin=(0.0, 0.0, 0.0),
+                   h=tuple(h), shear=tuple(shear), kf=kf, fault=fault, E=E, k=k, nu=0.25,
+                   alpha=0.8, M=50e9, mu_f=1e-3, fixed=fixed, fu=fu, fp=fp,
+                   dts=[dt] * steps, notes="small faulted box")
+
+
+def random_vectors(n_nodes: int, seed: int, scale_u: float = 1e-4, scale_p: float = 1e6):
+    """Seeded random (u, p) fields: u ~ U[-1,1] * scale_u (3, N), p ~ U[-1,1] * scale_p."""
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(-1.0, 1.0, (3, n_nodes)) * scale_u
+    p = rng.uniform(-1.0, 1.0, n_nodes) * scale_p
+    return u, p
+
+
+def random_displacement_jump(prob: Problem, seed: int, scale: float = 1e-6):
+    """A displacement field that is zero except on the upper fault lip, where it
+    is U[-1,1] * scale per component: prescribes arbitrary lip jumps."""
+    rng = np.random.default_rng(seed)
+    u = np.zeros((3, prob.n_nodes))
+    if prob.kf is not None:
+        nb = (prob.nx + 1) * (prob.ny + 1)
+        plus = slice((prob.kf + 1) * nb, (prob.kf + 2) * nb)
+        u[:, plus] = rng.uniform(-1.0, 1.0, (3, nb)) * scale
+    return u
+
+
+CONFIGS = {
+    "fault8": fault_small,
+    "slipfront64": slip_front,
+    "inclined160": inclined_lognormal,
+}
