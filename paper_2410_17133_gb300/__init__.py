@@ -1,0 +1,308 @@
+"""Python binding of libgm (include/gm.h): argument marshalling only.
+
+Every operator application, fault update, solve and time step runs in the CUDA
+library; this module converts torch tensors / numpy arrays to pointers and
+status codes to exceptions.  There is no CPU fallback: if the shared library is
+missing or fails to load, importing the binding raises.
+
+Device vectors are torch CUDA tensors (float64 or float32) laid out as the C
+ABI states: displacements (3, N) field-major, pressures (N,), coupled (4, N).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from ._build import LIB
+
+__all__ = ["lib", "GMError", "Solver", "OP", "OPEN", "STICK", "SLIP", "load_library"]
+
+OP = {"KB": 0, "KT": 1, "A22": 2, "APU": 3, "AUP": 4, "J": 5}
+OPEN, STICK, SLIP = 0, 1, 2
+F64, F32 = 0, 1
+
+
+class GMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"gm error {code}: {msg}")
+        self.code = code
+
+
+class FaultParams(C.Structure):
+    _fields_ = [("kn", C.c_double), ("ks", C.c_double), ("f", C.c_double), ("w0", C.c_double),
+                ("wk_par", C.c_double), ("k_perp", C.c_double), ("MF", C.c_double),
+                ("tn0", C.c_double), ("tau0", C.c_double * 2)]
+
+
+class SolveReport(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("rel_residual", C.c_double), ("status", C.c_int)]
+
+
+class StepOpts(C.Structure):
+    _fields_ = [("newton_rtol", C.c_double), ("newton_maxit", C.c_int),
+                ("outer_rtol", C.c_double), ("outer_maxit", C.c_int),
+                ("inner_rtol", C.c_double), ("inner_maxit", C.c_int),
+                ("precision", C.c_int)]
+
+
+class StepReport(C.Structure):
+    _fields_ = [("newton", C.c_int), ("outer", C.c_int), ("inner_k", C.c_longlong),
+                ("inner_a", C.c_longlong), ("applies", C.c_longlong), ("rhat", C.c_double),
+                ("rhat0", C.c_double), ("n_open", C.c_int), ("n_stick", C.c_int),
+                ("n_slip", C.c_int), ("min_yield_margin", C.c_double),
+                ("min_normal_margin", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_SIG = {
+    "gm_version": (C.c_char_p, []),
+    "gm_create": (C.c_int, [C.POINTER(_P), C.c_int]),
+    "gm_destroy": (C.c_int, [_P]),
+    "gm_last_error": (C.c_char_p, [_P]),
+    "gm_mesh_structured": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _D, _D, _D]),
+    "gm_fault_plane": (C.c_int, [_P, C.c_int, C.POINTER(FaultParams)]),
+    "gm_set_materials": (C.c_int, [_P, _D, _D, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "gm_set_dirichlet": (C.c_int, [_P, C.POINTER(C.c_uint8), C.c_int64]),
+    "gm_set_loads": (C.c_int, [_P, _D, _D]),
+    "gm_assemble_or_bind": (C.c_int, [_P]),
+    "gm_set_timestep": (C.c_int, [_P, C.c_double]),
+    "gm_apply_operator": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
+    "gm_fault_update": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "gm_pcg_solve": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int, C.POINTER(SolveReport), _P]),
+    "gm_prevost_solve": (C.c_int, [_P, _P, _P, C.c_double, C.c_int, C.c_double, C.c_int,
+                                   C.POINTER(SolveReport), _P]),
+    "gm_residual": (C.c_int, [_P, _P, _P, _P, _D, _P]),
+    "gm_partitioned_step": (C.c_int, [_P, C.c_double, C.POINTER(StepOpts), C.POINTER(StepReport), _P]),
+    "gm_get_state": (C.c_int, [_P, _D, _D, _D, _D, C.POINTER(C.c_int8)]),
+    "gm_set_state": (C.c_int, [_P, _D, _D, _D, C.POINTER(C.c_int8)]),
+    "gm_state_device": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P)]),
+    "gm_sizes": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB):
+    """Load libgm.so (built by __graft_entry__.build()).  Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libgm.so not found at {path}: build it with __graft_entry__.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIG.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def lib():
+    return load_library()
+
+
+def _dptr(a):
+    """Host float64 numpy array -> POINTER(c_double) (array must stay alive)."""
+    return a.ctypes.data_as(_D)
+
+
+def _tptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class Solver:
+    """One context: a structured grid, an optional fault plane, materials,
+    constraints and loads, bound on one GPU."""
+
+    def __init__(self, device: int = 0):
+        self._L = load_library()
+        h = _P()
+        rc = self._L.gm_create(C.byref(h), int(device))
+        if rc != 0:
+            raise GMError(rc, "gm_create failed")
+        self.h = h
+        self.device = device
+        self.N = self.n_el = self.P = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.gm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, rc):
+        if rc != 0:
+            msg = self._L.gm_last_error(self.h)
+            raise GMError(rc, msg.decode() if msg else "")
+        return rc
+
+    # -- set-up --------------------------------------------------------------
+    def mesh(self, nx, ny, nz, origin, h, shear=(0.0, 0.0)):
+        o = np.ascontiguousarray(origin, np.float64)
+        hh = np.ascontiguousarray(h, np.float64)
+        s = np.ascontiguousarray(shear, np.float64)
+        self._chk(self._L.gm_mesh_structured(self.h, nx, ny, nz, _dptr(o), _dptr(hh), _dptr(s)))
+
+    def fault(self, kf, kn, ks, f, w0, wk_par, k_perp, MF, tn0, tau0):
+        fp = FaultParams(kn, ks, f, w0, wk_par, k_perp, MF, tn0, (C.c_double * 2)(*tau0))
+        self._chk(self._L.gm_fault_plane(self.h, int(kf), C.byref(fp)))
+
+    def materials(self, E, k, nu, alpha, M, mu_f):
+        E = np.ascontiguousarray(np.atleast_1d(E), np.float64)
+        k = np.ascontiguousarray(np.broadcast_to(np.atleast_1d(k), E.shape), np.float64)
+        self._chk(self._L.gm_set_materials(self.h, _dptr(E), _dptr(k), E.size, nu, alpha, M, mu_f))
+
+    def dirichlet(self, fixed):
+        f = np.ascontiguousarray(fixed, np.uint8).reshape(-1)
+        self._chk(self._L.gm_set_dirichlet(self.h, f.ctypes.data_as(C.POINTER(C.c_uint8)), f.size))
+
+    def loads(self, fu=None, fp=None):
+        a = None if fu is None else np.ascontiguousarray(fu, np.float64).reshape(-1)
+        b = None if fp is None else np.ascontiguousarray(fp, np.float64).reshape(-1)
+        self._chk(self._L.gm_set_loads(self.h, None if a is None else _dptr(a),
+                                       None if b is None else _dptr(b)))
+
+    def bind(self):
+        self._chk(self._L.gm_assemble_or_bind(self.h))
+        n, e, p = C.c_int64(), C.c_int64(), C.c_int64()
+        self._chk(self._L.gm_sizes(self.h, C.byref(n), C.byref(e), C.byref(p)))
+        self.N, self.n_el, self.P = n.value, e.value, p.value
+
+    def timestep(self, dt):
+        self._chk(self._L.gm_set_timestep(self.h, float(dt)))
+
+    @classmethod
+    def from_problem(cls, prob, device: int = 0):
+        """Set up from any object with the attributes of a problem description
+        (nx, ny, nz, origin, h, shear, kf, fault, E, k, nu, alpha, M, mu_f,
+        fixed, fu, fp)."""
+        s = cls(device)
+        s.mesh(prob.nx, prob.ny, prob.nz, prob.origin, prob.h, prob.shear)
+        if prob.kf is not None:
+            fp = prob.fault
+            s.fault(prob.kf, fp.kn, fp.ks, fp.f, fp.w0, fp.wk_par, fp.k_perp, fp.MF, fp.tn0, fp.tau0)
+        E = np.asarray(prob.E, np.float64)
+        s.materials(E, np.broadcast_to(np.asarray(prob.k, np.float64), E.shape), prob.nu, prob.alpha,
+                    prob.M, prob.mu_f)
+        s.dirichlet(prob.fixed)
+        s.loads(prob.fu, prob.fp)
+        s.bind()
+        return s
+
+    # -- operators -------------------------------------------------------------
+    def apply(self, which, x, y=None, stream=None):
+        """y = A x for which in OP ('KB','KT','A22','APU','AUP','J'); x, y CUDA tensors."""
+        import torch
+        w = OP[which] if isinstance(which, str) else int(which)
+        N = self.N
+        shape_out = {0: (3, N), 1: (3, N), 2: (N,), 3: (3, N), 4: (N,), 5: (4, N)}[w]
+        if y is None:
+            y = torch.empty(shape_out, dtype=x.dtype, device=x.device)
+        dt = F64 if x.dtype == torch.float64 else F32
+        assert x.is_contiguous() and y.is_contiguous() and y.dtype == x.dtype
+        self._chk(self._L.gm_apply_operator(self.h, w, _tptr(x), _tptr(y), dt, _stream_ptr(stream)))
+        return y
+
+    def fault_update(self, u, stream=None):
+        """Return map at total displacement u (3, N) float64 CUDA tensor."""
+        import torch
+        P = self.P
+        dev = u.device
+        out = dict(flags=torch.empty(P, dtype=torch.int8, device=dev),
+                   tn=torch.empty(P, dtype=torch.float64, device=dev),
+                   ts=torch.empty((2, P), dtype=torch.float64, device=dev),
+                   dlie=torch.empty((2, P), dtype=torch.float64, device=dev),
+                   T=torch.empty((3, P), dtype=torch.float64, device=dev))
+        self._chk(self._L.gm_fault_update(self.h, _tptr(u), _tptr(out["flags"]), _tptr(out["tn"]),
+                                          _tptr(out["ts"]), _tptr(out["dlie"]), _tptr(out["T"]),
+                                          _stream_ptr(stream)))
+        return out
+
+    def pcg(self, which, b, x=None, rtol=1e-10, maxit=10000, stream=None):
+        import torch
+        w = OP[which] if isinstance(which, str) else int(which)
+        if x is None:
+            x = torch.zeros_like(b)
+        rep = SolveReport()
+        self._chk(self._L.gm_pcg_solve(self.h, w, _tptr(b), _tptr(x), rtol, maxit, C.byref(rep),
+                                       _stream_ptr(stream)))
+        return x, dict(iterations=rep.iterations, rel_residual=rep.rel_residual)
+
+    def prevost(self, b, outer_rtol=1e-10, outer_maxit=500, inner_rtol=1e-12, inner_maxit=20000,
+                stream=None):
+        import torch
+        x = torch.zeros_like(b)
+        rep = SolveReport()
+        self._chk(self._L.gm_prevost_solve(self.h, _tptr(b), _tptr(x), outer_rtol, outer_maxit,
+                                           inner_rtol, inner_maxit, C.byref(rep), _stream_ptr(stream)))
+        return x, dict(iterations=rep.iterations, rel_residual=rep.rel_residual)
+
+    def residual(self, du, dp, stream=None):
+        import torch
+        b = torch.empty((4, self.N), dtype=torch.float64, device=du.device)
+        rh = C.c_double()
+        self._chk(self._L.gm_residual(self.h, _tptr(du), _tptr(dp), _tptr(b), C.byref(rh),
+                                      _stream_ptr(stream)))
+        return b, rh.value
+
+    def step(self, dt, newton_rtol=None, precision=F64, newton_maxit=50, outer_rtol=None,
+             outer_maxit=500, inner_rtol=None, inner_maxit=20000, stream=None):
+        if newton_rtol is None and outer_rtol is None and inner_rtol is None and precision == F64:
+            opts = None
+        else:
+            d_outer = 1e-8 if precision == F64 else 1e-4
+            d_inner = 1e-10 if precision == F64 else 1e-5
+            opts = StepOpts(1e-10 if newton_rtol is None else newton_rtol, newton_maxit,
+                            d_outer if outer_rtol is None else outer_rtol, outer_maxit,
+                            d_inner if inner_rtol is None else inner_rtol, inner_maxit, precision)
+        rep = StepReport()
+        self._chk(self._L.gm_partitioned_step(self.h, float(dt), None if opts is None else C.byref(opts),
+                                              C.byref(rep), _stream_ptr(stream)))
+        return rep.as_dict()
+
+    # -- state -----------------------------------------------------------------
+    def get_state(self):
+        N, P = self.N, self.P
+        u = np.empty(3 * N)
+        p = np.empty(N)
+        slip = np.empty(max(2 * P, 1))
+        dlie = np.empty(max(2 * P, 1))
+        flags = np.empty(max(P, 1), np.int8)
+        self._chk(self._L.gm_get_state(self.h, _dptr(u), _dptr(p), _dptr(slip), _dptr(dlie),
+                                       flags.ctypes.data_as(C.POINTER(C.c_int8))))
+        return dict(u=u.reshape(3, N), p=p, slip=slip[:2 * P].reshape(2, P),
+                    dlie=dlie[:2 * P].reshape(2, P), flags=flags[:P])
+
+    def set_state(self, u=None, p=None, dlie=None, flags=None):
+        a = None if u is None else np.ascontiguousarray(u, np.float64).reshape(-1)
+        b = None if p is None else np.ascontiguousarray(p, np.float64).reshape(-1)
+        d = None if dlie is None else np.ascontiguousarray(dlie, np.float64).reshape(-1)
+        f = None if flags is None else np.ascontiguousarray(flags, np.int8).reshape(-1)
+        self._chk(self._L.gm_set_state(self.h, None if a is None else _dptr(a),
+                                       None if b is None else _dptr(b),
+                                       None if d is None else _dptr(d),
+                                       None if f is None else f.ctypes.data_as(C.POINTER(C.c_int8))))
+
+    def state_device(self):
+        """(u_ptr, p_ptr) raw device pointers of the accepted state."""
+        u, p = _P(), _P()
+        self._chk(self._L.gm_state_device(self.h, C.byref(u), C.byref(p)))
+        return u.value, p.value

@@ -1,0 +1,29 @@
+// FP32 instantiations of the matrix-free operator applies (mixed-precision path:
+// FP32 operator data, FP32 accumulation inside each element and node).
+#include "gm_apply.cuh"
+
+int gm_launch_apply_f32(gm_ctx* c, int mode, double cK, double cApu, double cAup, double cS,
+                        double cC, const float* xu, const float* xp, float* yu, float* yp,
+                        cudaStream_t s, const int* skip)
+{
+    const float* E = c->dE32.as<float>();
+    const float* kap = c->dK32.as<float>();
+    const float* D = c->dD32.as<float>();
+    const RefOps<float>& R = c->R32;
+#define GM_CASE(MD) \
+    case MD: gm_apply_dispatch_cls<float, MD>(c, R, cK, cApu, cAup, cS, cC, xu, xp, yu, yp, E, kap, D, s, skip); break;
+    switch (mode) {
+        GM_CASE(GM_MODE_K)
+        GM_CASE(GM_MODE_KT)
+        GM_CASE(GM_MODE_A22)
+        GM_CASE(GM_MODE_APU)
+        GM_CASE(GM_MODE_AUP)
+        GM_CASE(GM_MODE_J)
+    default:
+        return c->set_err(GM_EINVAL, "unsupported operator mode (fp32)");
+    }
+#undef GM_CASE
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return c->set_err(GM_ECUDA, std::string("apply launch: ") + cudaGetErrorString(e));
+    return GM_OK;
+}

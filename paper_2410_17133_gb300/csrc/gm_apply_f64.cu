@@ -1,0 +1,30 @@
+// FP64 instantiations of the matrix-free operator applies.
+#include "gm_apply.cuh"
+
+int gm_launch_apply_f64(gm_ctx* c, int mode, double cK, double cApu, double cAup, double cS,
+                        double cC, const double* xu, const double* xp, double* yu, double* yp,
+                        cudaStream_t s, const int* skip)
+{
+    const double* E = c->dE64.as<double>();
+    const double* kap = c->dK64.as<double>();
+    const double* D = c->dD64.as<double>();
+    const RefOps<double>& R = c->R64;
+#define GM_CASE(MD) \
+    case MD: gm_apply_dispatch_cls<double, MD>(c, R, cK, cApu, cAup, cS, cC, xu, xp, yu, yp, E, kap, D, s, skip); break;
+    switch (mode) {
+        GM_CASE(GM_MODE_K)
+        GM_CASE(GM_MODE_KT)
+        GM_CASE(GM_MODE_A22)
+        GM_CASE(GM_MODE_APU)
+        GM_CASE(GM_MODE_AUP)
+        GM_CASE(GM_MODE_J)
+        GM_CASE(GM_MODE_RES1)
+        GM_CASE(GM_MODE_RES2)
+    default:
+        return c->set_err(GM_EINVAL, "unsupported operator mode");
+    }
+#undef GM_CASE
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return c->set_err(GM_ECUDA, std::string("apply launch: ") + cudaGetErrorString(e));
+    return GM_OK;
+}

@@ -1,0 +1,279 @@
+// Matrix-free bulk operator kernel (Q1 hexahedra on an affine structured grid).
+//
+// Computes, for the operator blocks selected by MODE,
+//   y_u = cK E_e K_e u - cApu A_e p            (Sec. 3.2.1; App. A Eq. Apdp)
+//   y_p = cAup A_e^T u + cS S_e p + cC k_e L_e p   (Sec. 3.2.2; App. A Eq. Adpd)
+// summed over elements, the Ap-type products evaluated element by element and
+// gathered into the nodal vectors (Sec. 3.3.2).  All elements are the same
+// parallelepiped, so the element matrices are those of one reference cell
+// scaled by the element's E and k.  In the parity basis of the cell (the 8-point
+// Walsh-Hadamard transform of the nodal values, one per field) the reference
+// operators are block-diagonal by the cell's reflection symmetry; the kernel
+// transforms, multiplies block by block and transforms back.
+//
+// Work decomposition: a CTA of 16x16 threads owns 15x15 node columns and a
+// chunk of node planes; it marches up the planes.  Thread (tx, ty) handles the
+// element column (face) whose lower-left node is tile node (tx, ty), so each
+// element is computed exactly once inside the CTA, plus one halo column/row and
+// one halo layer that are recomputed by the neighbour.  The transform is split:
+// the xy part is done once per node plane per face and reused by the element
+// layers below and above the plane; the z part per element.  Element results
+// are accumulated per face in registers across the plane, then each node sums
+// its four faces from shared memory.  No atomics; results are deterministic.
+#pragma once
+
+#include "gm_internal.cuh"
+
+template <typename T, int CLS, int MODE>
+__global__ void __launch_bounds__(256)
+gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
+{
+    constexpr bool DO_K = (MODE & GM_M_K) != 0;
+    constexpr bool DO_APU = (MODE & GM_M_APU) != 0;
+    constexpr bool DO_AUP = (MODE & GM_M_AUP) != 0;
+    constexpr bool DO_S = (MODE & GM_M_S) != 0;
+    constexpr bool DO_C = (MODE & GM_M_C) != 0;
+    constexpr bool IN_U = DO_K || DO_AUP;
+    constexpr bool IN_P = DO_APU || DO_S || DO_C;
+    constexpr bool OUT_U = DO_K || DO_APU;
+    constexpr bool OUT_P = DO_AUP || DO_S || DO_C;
+    constexpr int NI = (IN_U ? 3 : 0) + (IN_P ? 1 : 0);
+    constexpr int NO = (OUT_U ? 3 : 0) + (OUT_P ? 1 : 0);
+    constexpr int IPI = IN_U ? 3 : 0;   // slot of p among the input fields
+    constexpr int OPI = OUT_U ? 3 : 0;  // slot of p among the output fields
+    constexpr SecTab ST = gm_make_sectab(CLS);
+    constexpr int NB = ST.nb, BU = ST.bu, BP = ST.bp;
+
+    if (a.skip != nullptr && *a.skip != 0) return;
+
+    __shared__ T s_plane[NI][17 * 17];
+    __shared__ T s_face[NO][4][256];
+
+    const GridDesc& g = a.g;
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int x0 = blockIdx.x * 15, y0 = blockIdx.y * 15;
+    const int fi = x0 - 1 + tx, fj = y0 - 1 + ty;
+    const bool fval = fi >= 0 && fi < g.nx && fj >= 0 && fj < g.ny;
+    const int z0 = blockIdx.z * a.zchunk;
+    const int z1 = min(z0 + a.zchunk, g.nplanes);
+    const long long N = g.N;
+    const long long rowlen = g.nx + 1;
+
+    // element layer between extended planes kb and kb+1 exists?
+    auto layer_exists = [&](int kb) -> bool {
+        return kb >= 0 && kb + 1 < g.nplanes && kb != g.kf;
+    };
+    auto layer_index = [&](int kb) -> int { return (g.kf >= 0 && kb > g.kf) ? kb - 1 : kb; };
+
+    auto load_plane = [&](int kk) {
+        for (int idx = tid; idx < 17 * 17; idx += 256) {
+            const int ni = idx % 17, nj = idx / 17;
+            const int gi = x0 - 1 + ni, gj = y0 - 1 + nj;
+            const bool ok = gi >= 0 && gi <= g.nx && gj >= 0 && gj <= g.ny;
+            const long long node = ok ? (gi + rowlen * (gj + (long long)(g.ny + 1) * kk)) : 0;
+            const unsigned m = ok ? a.mask[node] : 0xFu;
+            if constexpr (IN_U) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    s_plane[c][idx] = ((m >> c) & 1u) ? T(0) : a.xu[c * N + node];
+            }
+            if constexpr (IN_P) {
+                long long pn = node;
+                unsigned pm = m;
+                if (ok && g.tied && kk == g.kf + 1) {   // slave lip reads its master
+                    pn = node - g.nb;
+                    pm = a.mask[pn];
+                }
+                s_plane[IPI][idx] = ((pm >> 3) & 1u) ? T(0) : a.xp[pn];
+            }
+        }
+    };
+
+    // xy part of the forward transform for this thread's face:
+    // t[sx + 2 sy] = sum_{ax,ay} (-1)^(sx ax + sy ay) v[ax, ay]
+    auto fwd_xy = [&](T (&t)[NI][4]) {
+#pragma unroll
+        for (int f = 0; f < NI; ++f) {
+            const T v00 = s_plane[f][ty * 17 + tx], v10 = s_plane[f][ty * 17 + tx + 1];
+            const T v01 = s_plane[f][(ty + 1) * 17 + tx], v11 = s_plane[f][(ty + 1) * 17 + tx + 1];
+            const T a0 = v00 + v10, a1 = v00 - v10, b0 = v01 + v11, b1 = v01 - v11;
+            t[f][0] = a0 + b0;
+            t[f][1] = a1 + b1;
+            t[f][2] = a0 - b0;
+            t[f][3] = a1 - b1;
+        }
+    };
+
+    // One element: z part of the transform, sector products, inverse z part.
+    // ob/ot receive the xy-parity tuples of the bottom / top node sets.
+    auto element = [&](const T (&tb)[NI][4], const T (&tt)[NI][4], int kb, T (&ob)[NO][4],
+                       T (&ot)[NO][4]) {
+#pragma unroll
+        for (int f = 0; f < NO; ++f)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { ob[f][q] = T(0); ot[f][q] = T(0); }
+        const long long e = fi + (long long)g.nx * (fj + (long long)g.ny * layer_index(kb));
+        T kE = T(0), kC = T(0);
+        if constexpr (DO_K) kE = a.cK * a.E[e];
+        if constexpr (DO_C) kC = a.cC * a.kap[e];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            T xu[BU > 0 ? BU : 1];
+            T xp[BP > 0 ? BP : 1];
+            if constexpr (IN_U) {
+#pragma unroll
+                for (int k = 0; k < BU; ++k) {
+                    const int c = ST.uc[b][k], s = ST.us[b][k];
+                    xu[k] = (s & 4) ? (tb[c][s & 3] - tt[c][s & 3]) : (tb[c][s & 3] + tt[c][s & 3]);
+                }
+            }
+            if constexpr (IN_P) {
+#pragma unroll
+                for (int j = 0; j < BP; ++j) {
+                    const int s = ST.ps[b][j];
+                    xp[j] = (s & 4) ? (tb[IPI][s & 3] - tt[IPI][s & 3]) : (tb[IPI][s & 3] + tt[IPI][s & 3]);
+                }
+            }
+            if constexpr (OUT_U) {
+#pragma unroll
+                for (int k = 0; k < BU; ++k) {
+                    T acc = T(0);
+                    if constexpr (DO_K) {
+                        T t = T(0);
+#pragma unroll
+                        for (int k2 = 0; k2 < BU; ++k2) t = fma(R.K[(b * BU + k) * BU + k2], xu[k2], t);
+                        acc = kE * t;
+                    }
+                    if constexpr (DO_APU) {
+                        T t = T(0);
+#pragma unroll
+                        for (int j = 0; j < BP; ++j) t = fma(R.A[(b * BU + k) * BP + j], xp[j], t);
+                        acc = fma(a.cApu, t, acc);
+                    }
+                    const int c = ST.uc[b][k], s = ST.us[b][k];
+                    ob[c][s & 3] += acc;
+                    if (s & 4) ot[c][s & 3] -= acc; else ot[c][s & 3] += acc;
+                }
+            }
+            if constexpr (OUT_P) {
+#pragma unroll
+                for (int j = 0; j < BP; ++j) {
+                    T acc = T(0);
+                    if constexpr (DO_AUP) {
+                        T t = T(0);
+#pragma unroll
+                        for (int k = 0; k < BU; ++k) t = fma(R.A[(b * BU + k) * BP + j], xu[k], t);
+                        acc = a.cAup * t;
+                    }
+                    if constexpr (DO_S) {
+                        T t = T(0);
+#pragma unroll
+                        for (int j2 = 0; j2 < BP; ++j2) t = fma(R.M[(b * BP + j) * BP + j2], xp[j2], t);
+                        acc = fma(a.cS, t, acc);
+                    }
+                    if constexpr (DO_C) {
+                        T t = T(0);
+#pragma unroll
+                        for (int j2 = 0; j2 < BP; ++j2) t = fma(R.L[(b * BP + j) * BP + j2], xp[j2], t);
+                        acc = fma(kC, t, acc);
+                    }
+                    const int s = ST.ps[b][j];
+                    ob[OPI][s & 3] += acc;
+                    if (s & 4) ot[OPI][s & 3] -= acc; else ot[OPI][s & 3] += acc;
+                }
+            }
+        }
+    };
+
+    T tb[NI][4], tt[NI][4];
+    T carry[NO][4];
+#pragma unroll
+    for (int f = 0; f < NO; ++f)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) carry[f][q] = T(0);
+
+    // halo layer below the chunk (its top contributions complete plane z0)
+    if (layer_exists(z0 - 1)) {
+        load_plane(z0 - 1);
+        __syncthreads();
+        fwd_xy(tb);
+        __syncthreads();
+        load_plane(z0);
+        __syncthreads();
+        fwd_xy(tt);
+        if (fval) {
+            T ob[NO][4];
+            element(tb, tt, z0 - 1, ob, carry);
+        }
+#pragma unroll
+        for (int f = 0; f < NI; ++f)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) tb[f][q] = tt[f][q];
+    } else {
+        load_plane(z0);
+        __syncthreads();
+        fwd_xy(tb);
+    }
+
+    for (int kk = z0; kk < z1; ++kk) {
+        T ob[NO][4], ot[NO][4];
+#pragma unroll
+        for (int f = 0; f < NO; ++f)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { ob[f][q] = T(0); ot[f][q] = T(0); }
+        const bool up = layer_exists(kk);
+        if (up) {
+            __syncthreads();
+            load_plane(kk + 1);
+            __syncthreads();
+            fwd_xy(tt);
+            if (fval) element(tb, tt, kk, ob, ot);
+#pragma unroll
+            for (int f = 0; f < NI; ++f)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) tb[f][q] = tt[f][q];
+        } else if (kk + 1 < z1) {
+            // fault gap: the next plane starts a new block of elements
+            __syncthreads();
+            load_plane(kk + 1);
+            __syncthreads();
+            fwd_xy(tb);
+        }
+        // complete face tuples of plane kk, inverse xy transform to corner values
+        __syncthreads();
+#pragma unroll
+        for (int f = 0; f < NO; ++f) {
+            const T o0 = carry[f][0] + ob[f][0], o1 = carry[f][1] + ob[f][1];
+            const T o2 = carry[f][2] + ob[f][2], o3 = carry[f][3] + ob[f][3];
+            const T c0 = o0 + o1, c1 = o0 - o1, d0 = o2 + o3, d1 = o2 - o3;
+            s_face[f][0][tid] = c0 + d0;   // corner (0,0)
+            s_face[f][1][tid] = c1 + d1;   // corner (1,0)
+            s_face[f][2][tid] = c0 - d0;   // corner (0,1)
+            s_face[f][3][tid] = c1 - d1;   // corner (1,1)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) carry[f][q] = up ? ot[f][q] : T(0);
+        }
+        __syncthreads();
+        // node stage: node (tx, ty) of the tile sums its four faces
+        if (tx >= 1 && ty >= 1) {
+            const int gi = x0 - 1 + tx, gj = y0 - 1 + ty;
+            if (gi <= g.nx && gj <= g.ny) {
+                const long long node = gi + rowlen * (gj + (long long)(g.ny + 1) * kk);
+                const unsigned m = a.mask[node];
+#pragma unroll
+                for (int f = 0; f < NO; ++f) {
+                    const T v = s_face[f][0][tid] + s_face[f][1][tid - 1] +
+                                s_face[f][2][tid - 16] + s_face[f][3][tid - 17];
+                    if (OUT_U && f < 3) {
+                        a.yu[f * N + node] = ((m >> f) & 1u) ? T(0) : v;
+                    } else {
+                        // raw value on a tied slave lip: the fault kernel folds it
+                        const bool slave = g.tied && kk == g.kf + 1;
+                        a.yp[node] = (!slave && ((m >> 3) & 1u)) ? T(0) : v;
+                    }
+                }
+            }
+        }
+    }
+}

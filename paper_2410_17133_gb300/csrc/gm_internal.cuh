@@ -1,0 +1,308 @@
+// Internal declarations shared by the translation units of libgm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gm.h"
+
+// ---------------------------------------------------------------------------
+// Operator block selection for the matrix-free applies
+// ---------------------------------------------------------------------------
+enum : int {
+    GM_M_K = 1,      // bulk elasticity K_b
+    GM_M_APU = 2,    // pressure -> force coupling A_pu (bulk + fault lips)
+    GM_M_AUP = 4,    // displacement -> fluid-volume coupling A_up = A_pu^T
+    GM_M_S = 8,      // storage S (bulk consistent mass / M, fault w/M_F)
+    GM_M_C = 16,     // conductivity C (bulk k/mu, fault longitudinal + transverse)
+    GM_M_KF = 32     // fault tangent (cohesive stiffness)
+};
+// Modes used by the solvers (bit sets of the above)
+enum : int {
+    GM_MODE_K = GM_M_K,                                         // K_b
+    GM_MODE_KT = GM_M_K | GM_M_KF,                              // K_T
+    GM_MODE_A22 = GM_M_S | GM_M_C,                              // S + dt C
+    GM_MODE_APU = GM_M_APU,
+    GM_MODE_AUP = GM_M_AUP,
+    GM_MODE_J = GM_M_K | GM_M_KF | GM_M_APU | GM_M_AUP | GM_M_S | GM_M_C,
+    GM_MODE_RES1 = GM_M_K | GM_M_APU | GM_M_C,                  // K_b u - A_pu p, dt C p
+    GM_MODE_RES2 = GM_M_AUP | GM_M_S                            // A_up du + S dp
+};
+
+// Symmetry classes of the affine cell (number of parity sectors).
+enum : int { GM_CLS_BOX = 0, GM_CLS_MONO = 1, GM_CLS_GEN = 2 };
+
+// ---------------------------------------------------------------------------
+// Reference-cell operators in the parity (Walsh-Hadamard) basis, packed by
+// sector.  For class nb sectors, bu = 24/nb displacement entries and
+// bp = 8/nb pressure entries per sector.
+//   K[b][k][k'] (bu x bu)  for E = 1
+//   A[b][k][j]  (bu x bp)  for alpha = 1
+//   M[b][j][j'], L[b][j][j'] (bp x bp) for 1/M = 1 and k/mu = 1
+// All already carry the 1/64 of the inverse transform.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct RefOps {
+    T K[288];
+    T A[96];
+    T M[32];
+    T L[32];
+};
+
+// Sector membership, computed at compile time from the class.
+struct SecTab {
+    int nb, bu, bp;
+    int uc[8][12];
+    int us[8][12];
+    int ps[8][4];
+};
+
+__host__ __device__ constexpr int gm_popc3(int s) { return (s & 1) + ((s >> 1) & 1) + ((s >> 2) & 1); }
+
+// Character labels of the reflection group of the cell.  u_c at parity index s
+// transforms like s XOR e_c under the three mirror planes of a box; a cell
+// sheared in x-z keeps the y mirror and the central inversion; a general
+// parallelepiped keeps only the inversion.
+__host__ __device__ constexpr int gm_ulabel(int cls, int c, int s) {
+    return cls == GM_CLS_BOX ? (s ^ (1 << c))
+         : cls == GM_CLS_MONO ? ((((s >> 1) & 1) ^ (c == 1 ? 1 : 0)) + 2 * (1 ^ (gm_popc3(s) & 1)))
+                              : (1 ^ (gm_popc3(s) & 1));
+}
+__host__ __device__ constexpr int gm_plabel(int cls, int s) {
+    return cls == GM_CLS_BOX ? s
+         : cls == GM_CLS_MONO ? (((s >> 1) & 1) + 2 * (gm_popc3(s) & 1))
+                              : (gm_popc3(s) & 1);
+}
+__host__ __device__ constexpr SecTab gm_make_sectab(int cls) {
+    SecTab t{};
+    t.nb = cls == GM_CLS_BOX ? 8 : (cls == GM_CLS_MONO ? 4 : 2);
+    t.bu = 24 / t.nb;
+    t.bp = 8 / t.nb;
+    for (int b = 0; b < t.nb; ++b) {
+        int k = 0;
+        for (int c = 0; c < 3; ++c)
+            for (int s = 0; s < 8; ++s)
+                if (gm_ulabel(cls, c, s) == b) { t.uc[b][k] = c; t.us[b][k] = s; ++k; }
+        int j = 0;
+        for (int s = 0; s < 8; ++s)
+            if (gm_plabel(cls, s) == b) { t.ps[b][j] = s; ++j; }
+    }
+    return t;
+}
+
+// Per-node mask bits: 1,2,4 = ux,uy,uz fixed, 8 = p fixed.
+// Tied upper-lip pressures are slaves (handled by index, not by this mask).
+
+// ---------------------------------------------------------------------------
+// Kernel argument blocks
+// ---------------------------------------------------------------------------
+struct GridDesc {
+    int nx, ny, nz, nplanes;
+    int kf;          // lower-lip extended plane, -1 without fault
+    int tied;        // 1: upper-lip pressures slaved to lower lip
+    long long N;     // nodes
+    long long nb;    // nodes per plane
+};
+
+template <typename T>
+struct BulkArgs {
+    GridDesc g;
+    int zchunk;
+    const T* xu;     // 3N (or null)
+    const T* xp;     // N  (or null)
+    T* yu;
+    T* yp;
+    const T* E;      // per element
+    const T* kap;    // per element k / mu_f
+    const uint8_t* mask;
+    T cK, cApu, cAup, cS, cC;   // alpha and 1/M folded in by the host
+    const int* skip; // if non-null and *skip != 0 the kernel returns at once
+};
+
+template <typename T>
+struct FaultArgs {
+    GridDesc g;
+    const T* xu;
+    const T* xp;
+    T* yu;
+    T* yp;
+    const T* D;      // 6 per pair, field-major: D00 D01 D02 D11 D12 D22
+    const uint8_t* mask;
+    T cKf, cApu, cAup, cS, cC;
+    T Aq;            // area of one fault quad
+    T n[3];          // unit normal, lower -> upper lip
+    T stor;          // w0 / M_F
+    T lcoef;         // wk_par / mu_f
+    T tcoef;         // k_perp / (mu_f w0)
+    T Lf[16];        // reference quad Laplacian (coefficient 1)
+    const int* skip;
+};
+
+struct LawArgs {
+    GridDesc g;
+    const double* un;        // accepted displacement (3N)
+    const double* du;        // increment (3N) or null
+    const double* dlie_prev; // 2P
+    const double* fpair;     // per-pair friction or null
+    double kn, ks, f, tn0, tau0[2];
+    double n[3], t1[3], t2[3];
+    double Aq;
+    int8_t* state;
+    double* tn;
+    double* ts;              // 2P
+    double* dlie;            // 2P
+    double* T;               // 3P (incremental conjugate traction)
+    double* F;               // P (trial yield value)
+    double* dn;              // P (n.[[u]])
+    double* gs;              // 2P (P_t [[u]] in the fault frame)
+    double* D64;             // 6P
+    float* D32;              // 6P (or null)
+};
+
+struct PcgScalars {
+    double rz, pq, alpha, beta, rr, rr0, tol2, pad;
+    int it, done, status, pad2;
+};
+
+// ---------------------------------------------------------------------------
+// Device buffer
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    cudaError_t alloc(size_t bytes) {
+        release();
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e == cudaSuccess) n = bytes;
+        else p = nullptr;
+        return e;
+    }
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct gm_ctx {
+    int device = 0;
+    std::string err;
+    int sm_count = 152;
+
+    // set-up
+    bool has_mesh = false, has_fault = false, has_mat = false, bound = false;
+    int nx = 0, ny = 0, nz = 0;
+    double origin[3] = {0, 0, 0}, h[3] = {1, 1, 1}, shear[2] = {0, 0};
+    int kf_orig = -1;
+    gm_fault_params fp{};
+    std::vector<double> E, kperm;
+    double nu = 0.25, alpha = 1.0, M = 1.0, mu_f = 1.0;
+    std::vector<uint8_t> fixed;   // 4N
+    std::vector<double> fu, fpv;  // 3N, N
+
+    // derived
+    GridDesc g{};
+    long long N = 0, n_el = 0, P = 0;
+    int cls = GM_CLS_BOX;
+    RefOps<double> R64{};
+    RefOps<float> R32{};
+    double Kblk_ref[8][9] = {};   // nodal 3x3 diagonal blocks of K_ref (E = 1)
+    double Mdiag_ref[8] = {}, Ldiag_ref[8] = {};
+    double Aq = 0, nrm[3] = {0, 0, 1}, t1[3] = {1, 0, 0}, t2[3] = {0, 1, 0};
+    double Lf[16] = {};
+    double dt = 1.0;
+    double f0sq = 0.0;            // sum F0^2 / diag(K_b) over free lip dofs
+
+    // device data
+    DevBuf dE64, dK64, dE32, dK32, dmask, dfu, dfp;
+    DevBuf du_n, dp_n, ddlie_n, dflags_n;              // accepted state
+    DevBuf dstate, dtn, dts, ddlie, dT, dF, ddn, dgs, dD64, dD32;   // fault work
+    DevBuf ddiagK, ddiagA, dKinv64, dKinv32, dAinv64, dAinv32;
+    DevBuf dscal;                                      // PcgScalars[4] + misc
+    DevBuf dpart;                                      // reduction partials
+    DevBuf dcount;                                     // last-block counters
+    // work vectors (FP64)
+    DevBuf w_du, w_dp, w_ut, w_pt, w_b, w_x, w_y1u, w_y1p, w_y2u, w_y2p;
+    DevBuf k_r, k_z, k_p, k_q, a_r, a_z, a_p, a_q;     // inner PCG (FP64)
+    DevBuf k_r32, k_z32, k_p32, k_q32, k_x32, k_b32;   // inner PCG (FP32)
+    DevBuf a_r32, a_z32, a_p32, a_q32, a_x32, a_b32;
+    DevBuf o_y1, o_w, o_x1, o_t3, o_r, o_z, o_zold, o_p, o_q, o_x2, o_t1;   // outer CG
+    DevBuf dprevstate;
+    void* hpin = nullptr;                              // pinned host scratch (4 KB)
+    long long applies = 0;                             // bulk apply launches
+
+    int set_err(int code, const std::string& msg) {
+        err = msg;
+        return code;
+    }
+};
+
+#define GM_CUDA_TRY(ctx, call)                                                        \
+    do {                                                                              \
+        cudaError_t _e = (call);                                                      \
+        if (_e != cudaSuccess)                                                        \
+            return (ctx)->set_err(GM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+// Matrix-free operator application: bulk kernel then fault kernel.
+int gm_launch_apply_f64(gm_ctx* c, int mode, double cK, double cApu, double cAup, double cS,
+                        double cC, const double* xu, const double* xp, double* yu, double* yp,
+                        cudaStream_t s, const int* skip);
+int gm_launch_apply_f32(gm_ctx* c, int mode, double cK, double cApu, double cAup, double cS,
+                        double cC, const float* xu, const float* xp, float* yu, float* yp,
+                        cudaStream_t s, const int* skip);
+
+// Fault law, residual, preconditioners
+int gm_launch_return_map(gm_ctx* c, const double* un, const double* du, cudaStream_t s);
+int gm_launch_residual(gm_ctx* c, const double* y1u, const double* y1p, const double* y2p,
+                       const double* ut, const double* pt, double* b, cudaStream_t s,
+                       double* out2 /* device: rhat^2, shat^2 */);
+int gm_launch_diag(gm_ctx* c, cudaStream_t s);            // dK (bulk), dA (needs dt)
+int gm_launch_block_jacobi(gm_ctx* c, cudaStream_t s);    // K_T 3x3 inverse blocks
+int gm_launch_count_changes(gm_ctx* c, const int8_t* a, const int8_t* b, int* out, cudaStream_t s);
+
+// Linear algebra
+int gm_launch_pcg_init(gm_ctx* c, int which, int prec, const void* b, const void* q, void* r,
+                       void* z, void* p, double rtol, PcgScalars* sc, cudaStream_t s);
+int gm_launch_pcg_alpha(gm_ctx* c, int which, int prec, const void* p, const void* q,
+                        PcgScalars* sc, cudaStream_t s);
+int gm_launch_pcg_update(gm_ctx* c, int which, int prec, void* x, void* r, void* z,
+                         const void* p, const void* q, PcgScalars* sc, int maxit, cudaStream_t s);
+int gm_launch_pcg_dir(gm_ctx* c, int which, int prec, void* p, const void* z, PcgScalars* sc,
+                      cudaStream_t s);
+// y = a*x + b*y over n doubles; z = x + y etc.
+int gm_launch_axpby(gm_ctx* c, long long n, double a, const double* x, double b, double* y,
+                    cudaStream_t s);
+int gm_launch_copy_cast_d2f(gm_ctx* c, long long n, const double* x, float* y, cudaStream_t s);
+int gm_launch_copy_cast_f2d(gm_ctx* c, long long n, const float* x, double* y, cudaStream_t s);
+int gm_launch_axpy_f2d(gm_ctx* c, long long n, double a, const float* x, double* y, cudaStream_t s);
+// Deterministic dot products: out[0] = x.y (and out[1] = x2.y2 if x2) as doubles
+int gm_launch_dot(gm_ctx* c, long long n, const double* x, const double* y, const double* x2,
+                  const double* y2, double* out, cudaStream_t s);
+int gm_launch_jacobi_apply(gm_ctx* c, int which, const double* r, double* z, cudaStream_t s);
+
+// Solvers (gm_solve.cu)
+int gm_pcg(gm_ctx* c, int which, int prec, const double* b, double* x, double rtol, int maxit,
+           int* iters, double* relres, cudaStream_t s);
+int gm_prevost(gm_ctx* c, int prec, const double* b1, const double* b2, double* x1, double* x2,
+               double outer_rtol, int outer_maxit, double inner_rtol, int inner_maxit,
+               int* outer_it, long long* inner_k, long long* inner_a, double* relres,
+               cudaStream_t s);
+
+constexpr int GM_RED_BLOCKS = 608;   // fixed grid of the deterministic reductions
+constexpr int GM_RED_THREADS = 256;

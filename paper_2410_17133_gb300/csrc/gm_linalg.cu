@@ -1,0 +1,436 @@
+// Preconditioned-CG vector kernels with fused, deterministic FP64 reductions.
+//
+// One PCG iteration (Hestenes-Stiefel, as used inside the partitioned scheme of
+// Sec. 3.3.2) is: q = A p (apply kernels);  alpha = (r.z)/(p.q);
+// x += alpha p, r -= alpha q, z = M^-1 r with the new r.z and r.r in the same
+// pass;  beta = (r.z)_new/(r.z);  p = z + beta p.  The scalars live on the
+// device (PcgScalars) so iterations can be enqueued back to back; every kernel
+// returns at once when `done` is set, so the host only checks now and then.
+// Vectors may be FP32 (mixed precision) or FP64; dots always accumulate in FP64.
+#include "gm_internal.cuh"
+
+template <int NV>
+__device__ void gm_block_sum_l(double (&v)[NV], double* sh)
+{
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[k * 32 + w] = v[k];
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            v[k] = lane < nw ? sh[k * 32 + lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+        }
+    }
+}
+
+template <int NV>
+__device__ bool gm_grid_sum_l(double (&v)[NV], double* part, unsigned* counter)
+{
+    __shared__ double sh[NV * 32];
+    __shared__ bool last;
+    gm_block_sum_l<NV>(v, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) part[k * gridDim.x + blockIdx.x] = v[k];
+        __threadfence();
+        const unsigned t = atomicAdd(counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        acc[k] = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+            acc[k] += ((volatile double*)part)[k * gridDim.x + b];
+    }
+    __syncthreads();
+    gm_block_sum_l<NV>(acc, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = acc[k];
+        *counter = 0u;
+    }
+    return threadIdx.x == 0;
+}
+
+// Preconditioner application for one node.  WHICH 0: 3 components, 3x3
+// symmetric block inverse (6 per node);  WHICH 1: 1 component, diagonal inverse.
+template <typename T, int WHICH>
+struct Prec;
+template <typename T>
+struct Prec<T, 0> {
+    static constexpr int NC = 3;
+    __device__ static void apply(const T* mi, long long N, long long n, const double (&r)[3], double (&z)[3]) {
+        const double i0 = mi[n], i1 = mi[N + n], i2 = mi[2 * N + n];
+        const double i3 = mi[3 * N + n], i4 = mi[4 * N + n], i5 = mi[5 * N + n];
+        z[0] = i0 * r[0] + i1 * r[1] + i2 * r[2];
+        z[1] = i1 * r[0] + i3 * r[1] + i4 * r[2];
+        z[2] = i2 * r[0] + i4 * r[1] + i5 * r[2];
+    }
+};
+template <typename T>
+struct Prec<T, 1> {
+    static constexpr int NC = 1;
+    __device__ static void apply(const T* mi, long long, long long n, const double (&r)[1], double (&z)[1]) {
+        z[0] = (double)mi[n] * r[0];
+    }
+};
+
+struct RedCtx {
+    double* part;
+    unsigned* counter;
+};
+
+template <typename T, int WHICH>
+__global__ void __launch_bounds__(256)
+gm_pcg_init_kernel(long long N, const T* b, const T* q, T* r, T* z, T* p, const T* mi, double rtol,
+                   PcgScalars* sc, RedCtx rc)
+{
+    constexpr int NC = Prec<T, WHICH>::NC;
+    double v[2] = {0.0, 0.0};
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        double rr[NC], zz[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const double bq = (double)b[c * N + n] - (q ? (double)q[c * N + n] : 0.0);
+            rr[c] = (double)(T)bq;
+        }
+        Prec<T, WHICH>::apply(mi, N, n, rr, zz);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const T zt = (T)zz[c];
+            r[c * N + n] = (T)rr[c];
+            z[c * N + n] = zt;
+            p[c * N + n] = zt;
+            v[0] += rr[c] * (double)zt;
+            v[1] += rr[c] * rr[c];
+        }
+    }
+    if (gm_grid_sum_l<2>(v, rc.part, rc.counter)) {
+        sc->rz = v[0];
+        sc->rr = v[1];
+        sc->rr0 = v[1];
+        sc->tol2 = rtol * rtol * v[1];
+        sc->it = 0;
+        sc->status = (isfinite(v[0]) && isfinite(v[1])) ? GM_OK : GM_ENAN;
+        sc->done = (v[1] == 0.0 || sc->status != GM_OK) ? 1 : 0;
+        sc->alpha = 0.0;
+        sc->beta = 0.0;
+    }
+}
+
+template <typename T, int WHICH>
+__global__ void __launch_bounds__(256)
+gm_pcg_alpha_kernel(long long N, const T* p, const T* q, PcgScalars* sc, RedCtx rc)
+{
+    constexpr int NC = Prec<T, WHICH>::NC;
+    if (sc->done) return;
+    double v[1] = {0.0};
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) v[0] += (double)p[c * N + n] * (double)q[c * N + n];
+    if (gm_grid_sum_l<1>(v, rc.part, rc.counter)) {
+        sc->pq = v[0];
+        if (!(v[0] > 0.0) || !isfinite(v[0])) {
+            sc->status = isfinite(v[0]) ? GM_ENOCONV : GM_ENAN;
+            sc->done = 1;
+            sc->alpha = 0.0;
+        } else {
+            sc->alpha = sc->rz / v[0];
+        }
+    }
+}
+
+template <typename T, int WHICH>
+__global__ void __launch_bounds__(256)
+gm_pcg_update_kernel(long long N, T* x, T* r, T* z, const T* p, const T* q, const T* mi,
+                     PcgScalars* sc, int maxit, RedCtx rc)
+{
+    constexpr int NC = Prec<T, WHICH>::NC;
+    if (sc->done) return;
+    const double alpha = sc->alpha;
+    double v[2] = {0.0, 0.0};
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        double rr[NC], zz[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const long long k = c * N + n;
+            const double pk = (double)p[k];
+            x[k] = (T)((double)x[k] + alpha * pk);
+            rr[c] = (double)(T)((double)r[k] - alpha * (double)q[k]);
+            r[k] = (T)rr[c];
+        }
+        Prec<T, WHICH>::apply(mi, N, n, rr, zz);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const T zt = (T)zz[c];
+            z[c * N + n] = zt;
+            v[0] += rr[c] * (double)zt;
+            v[1] += rr[c] * rr[c];
+        }
+    }
+    if (gm_grid_sum_l<2>(v, rc.part, rc.counter)) {
+        sc->it += 1;
+        sc->rr = v[1];
+        if (!isfinite(v[0]) || !isfinite(v[1])) {
+            sc->status = GM_ENAN;
+            sc->done = 1;
+        } else if (v[1] <= sc->tol2) {
+            sc->done = 1;
+        } else if (sc->it >= maxit) {
+            sc->status = GM_ENOCONV;
+            sc->done = 1;
+        } else {
+            sc->beta = v[0] / sc->rz;
+            sc->rz = v[0];
+        }
+    }
+}
+
+template <typename T, int WHICH>
+__global__ void __launch_bounds__(256)
+gm_pcg_dir_kernel(long long N, T* p, const T* z, const PcgScalars* sc)
+{
+    constexpr int NC = Prec<T, WHICH>::NC;
+    if (sc->done) return;
+    const double beta = sc->beta;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const long long k = c * N + n;
+            p[k] = (T)((double)z[k] + beta * (double)p[k]);
+        }
+}
+
+static RedCtx redctx(gm_ctx* c)
+{
+    return RedCtx{c->dpart.as<double>(), c->dcount.as<unsigned>()};
+}
+
+// which: 0 = K_T (3 comps), 1 = A22; prec: GM_F64 / GM_F32
+#define GM_PCG_DISPATCH(KERNEL, ...)                                                          \
+    do {                                                                                      \
+        if (prec == GM_F64) {                                                                 \
+            if (which == 0) KERNEL<double, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(__VA_ARGS__); \
+            else KERNEL<double, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(__VA_ARGS__);   \
+        } else {                                                                              \
+            if (which == 0) KERNEL<float, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(__VA_ARGS__); \
+            else KERNEL<float, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(__VA_ARGS__);    \
+        }                                                                                     \
+    } while (0)
+
+template <typename T>
+static const T* prec_ptr(gm_ctx* c, int which)
+{
+    if constexpr (sizeof(T) == 8) return which == 0 ? c->dKinv64.as<T>() : c->dAinv64.as<T>();
+    else return which == 0 ? c->dKinv32.as<T>() : c->dAinv32.as<T>();
+}
+
+int gm_launch_pcg_init(gm_ctx* c, int which, int prec, const void* b, const void* q, void* r,
+                       void* z, void* p, double rtol, PcgScalars* sc, cudaStream_t s)
+{
+    const long long N = c->N;
+    RedCtx rc = redctx(c);
+    if (prec == GM_F64) {
+        if (which == 0)
+            gm_pcg_init_kernel<double, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
+                N, (const double*)b, (const double*)q, (double*)r, (double*)z, (double*)p,
+                prec_ptr<double>(c, 0), rtol, sc, rc);
+        else
+            gm_pcg_init_kernel<double, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
+                N, (const double*)b, (const double*)q, (double*)r, (double*)z, (double*)p,
+                prec_ptr<double>(c, 1), rtol, sc, rc);
+    } else {
+        if (which == 0)
+            gm_pcg_init_kernel<float, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
+                N, (const float*)b, (const float*)q, (float*)r, (float*)z, (float*)p,
+                prec_ptr<float>(c, 0), rtol, sc, rc);
+        else
+            gm_pcg_init_kernel<float, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
+                N, (const float*)b, (const float*)q, (float*)r, (float*)z, (float*)p,
+                prec_ptr<float>(c, 1), rtol, sc, rc);
+    }
+    GM_CUDA_TRY(c, cudaGetLastError());
+    return GM_OK;
+}
+
+int gm_launch_pcg_alpha(gm_ctx* c, int which, int prec, const void* p, const void* q,
+                        PcgScalars* sc, cudaStream_t s)
+{
+    const long long N = c->N;
+    RedCtx rc = redctx(c);
+    if (prec == GM_F64) {
+        if (which == 0) gm_pcg_alpha_kernel<double, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (const double*)p, (const double*)q, sc, rc);
+        else gm_pcg_alpha_kernel<double, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (const double*)p, (const double*)q, sc, rc);
+    } else {
+        if (which == 0) gm_pcg_alpha_kernel<float, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (const float*)p, (const float*)q, sc, rc);
+        else gm_pcg_alpha_kernel<float, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (const float*)p, (const float*)q, sc, rc);
+    }
+    GM_CUDA_TRY(c, cudaGetLastError());
+    return GM_OK;
+}
+
+int gm_launch_pcg_update(gm_ctx* c, int which, int prec, void* x, void* r, void* z, const void* p,
+                         const void* q, PcgScalars* sc, int maxit, cudaStream_t s)
+{
+    const long long N = c->N;
+    RedCtx rc = redctx(c);
+    if (prec == GM_F64) {
+        if (which == 0)
+            gm_pcg_update_kernel<double, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
+                N, (double*)x, (double*)r, (double*)z, (const double*)p, (const double*)q,
+                prec_ptr<double>(c, 0), sc, maxit, rc);
+        else
+            gm_pcg_update_kernel<double, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
+                N, (double*)x, (double*)r, (double*)z, (const double*)p, (const double*)q,
+                prec_ptr<double>(c, 1), sc, maxit, rc);
+    } else {
+        if (which == 0)
+            gm_pcg_update_kernel<float, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
+                N, (float*)x, (float*)r, (float*)z, (const float*)p, (const float*)q,
+                prec_ptr<float>(c, 0), sc, maxit, rc);
+        else
+            gm_pcg_update_kernel<float, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
+                N, (float*)x, (float*)r, (float*)z, (const float*)p, (const float*)q,
+                prec_ptr<float>(c, 1), sc, maxit, rc);
+    }
+    GM_CUDA_TRY(c, cudaGetLastError());
+    return GM_OK;
+}
+
+int gm_launch_pcg_dir(gm_ctx* c, int which, int prec, void* p, const void* z, PcgScalars* sc,
+                      cudaStream_t s)
+{
+    const long long N = c->N;
+    if (prec == GM_F64) {
+        if (which == 0) gm_pcg_dir_kernel<double, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (double*)p, (const double*)z, sc);
+        else gm_pcg_dir_kernel<double, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (double*)p, (const double*)z, sc);
+    } else {
+        if (which == 0) gm_pcg_dir_kernel<float, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (float*)p, (const float*)z, sc);
+        else gm_pcg_dir_kernel<float, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (float*)p, (const float*)z, sc);
+    }
+    GM_CUDA_TRY(c, cudaGetLastError());
+    return GM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Generic vector kernels
+// ---------------------------------------------------------------------------
+__global__ void gm_axpby_kernel(long long n, double a, const double* x, double b, double* y)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = a * x[i] + (b == 0.0 ? 0.0 : b * y[i]);
+}
+
+int gm_launch_axpby(gm_ctx* c, long long n, double a, const double* x, double b, double* y,
+                    cudaStream_t s)
+{
+    gm_axpby_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(n, a, x, b, y);
+    GM_CUDA_TRY(c, cudaGetLastError());
+    return GM_OK;
+}
+
+__global__ void gm_d2f_kernel(long long n, const double* x, float* y)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
+}
+__global__ void gm_f2d_kernel(long long n, const float* x, double* y)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = (double)x[i];
+}
+__global__ void gm_axpy_f2d_kernel(long long n, double a, const float* x, double* y)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] += a * (double)x[i];
+}
+
+int gm_launch_copy_cast_d2f(gm_ctx* c, long long n, const double* x, float* y, cudaStream_t s)
+{
+    gm_d2f_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(n, x, y);
+    GM_CUDA_TRY(c, cudaGetLastError());
+    return GM_OK;
+}
+int gm_launch_copy_cast_f2d(gm_ctx* c, long long n, const float* x, double* y, cudaStream_t s)
+{
+    gm_f2d_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(n, x, y);
+    GM_CUDA_TRY(c, cudaGetLastError());
+    return GM_OK;
+}
+int gm_launch_axpy_f2d(gm_ctx* c, long long n, double a, const float* x, double* y, cudaStream_t s)
+{
+    gm_axpy_f2d_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(n, a, x, y);
+    GM_CUDA_TRY(c, cudaGetLastError());
+    return GM_OK;
+}
+
+__global__ void __launch_bounds__(256)
+gm_dot_kernel(long long n, const double* x, const double* y, const double* x2, const double* y2,
+              double* out, RedCtx rc)
+{
+    double v[2] = {0.0, 0.0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        v[0] += x[i] * y[i];
+        if (x2) v[1] += x2[i] * y2[i];
+    }
+    if (gm_grid_sum_l<2>(v, rc.part, rc.counter)) {
+        out[0] = v[0];
+        out[1] = v[1];
+    }
+}
+
+int gm_launch_dot(gm_ctx* c, long long n, const double* x, const double* y, const double* x2,
+                  const double* y2, double* out, cudaStream_t s)
+{
+    gm_dot_kernel<<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(n, x, y, x2, y2, out, redctx(c));
+    GM_CUDA_TRY(c, cudaGetLastError());
+    return GM_OK;
+}
+
+// z = M^-1 r (outer-loop preconditioner application, FP64)
+template <int WHICH>
+__global__ void gm_jacobi_apply_kernel(long long N, const double* mi, const double* r, double* z)
+{
+    constexpr int NC = Prec<double, WHICH>::NC;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        double rr[NC], zz[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) rr[c] = r[c * N + n];
+        Prec<double, WHICH>::apply(mi, N, n, rr, zz);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) z[c * N + n] = zz[c];
+    }
+}
+
+int gm_launch_jacobi_apply(gm_ctx* c, int which, const double* r, double* z, cudaStream_t s)
+{
+    if (which == 0)
+        gm_jacobi_apply_kernel<0><<<GM_RED_BLOCKS, 256, 0, s>>>(c->N, c->dKinv64.as<double>(), r, z);
+    else
+        gm_jacobi_apply_kernel<1><<<GM_RED_BLOCKS, 256, 0, s>>>(c->N, c->dAinv64.as<double>(), r, z);
+    GM_CUDA_TRY(c, cudaGetLastError());
+    return GM_OK;
+}

@@ -1,0 +1,37 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/gm.h declares (no GPU needed; no compute calls)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "gm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(gm_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_library_exports_header_symbols():
+    from paper_2410_17133_gb300 import _build
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    syms = declared_symbols()
+    assert len(syms) >= 20
+    missing = [s for s in syms if not hasattr(lib, s)]
+    assert not missing, missing
+    lib.gm_version.restype = ctypes.c_char_p
+    assert lib.gm_version().startswith(b"gm-gb300")
+
+
+def test_binding_refuses_missing_library(tmp_path):
+    import pytest
+    import paper_2410_17133_gb300 as gm
+    saved = gm._lib
+    gm._lib = None
+    try:
+        with pytest.raises(ImportError):
+            gm.load_library(str(tmp_path / "nope.so"))
+    finally:
+        gm._lib = saved

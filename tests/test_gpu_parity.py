@@ -1,0 +1,227 @@
+"""GPU path vs the CPU oracle, element by element, on seeded inputs.
+
+Sizes span several 15x15 node tiles with ragged edges, plane chunks that start
+at either fault lip, the box and both sheared cell classes, tied and double-node
+pressures, and a fault-free grid.  FP64 operator applies must agree to 1e-12
+(relative L2), solves to their tolerances, implicit steps to 1e-9 with
+identical fault states (the 1e-9 bound is the FP64 parity target)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fem, solve as osolve
+
+from gpu_common import cuda, need_gpu, rel, solver_for, torch
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "box_tied_8": lambda: W.fault_small(),
+    "ragged_tied": lambda: W.tiny_faulted(17, 16, 6, seed=5, h=(0.4, 0.3, 0.5)),
+    "chunk_at_upper_lip": lambda: W.tiny_faulted(16, 3, 6, seed=6),
+    "sheared_x_untied": lambda: W.tiny_faulted(9, 7, 6, shear=(1.7320508075688772, 0.0), k_perp=1e-13, seed=7),
+    "sheared_xy_tied": lambda: W.tiny_faulted(6, 5, 4, shear=(0.4, -0.3), seed=8),
+    "no_fault": lambda: _nofault(),
+}
+
+
+def _nofault():
+    p = W.tiny_faulted(18, 5, 7, seed=9)
+    p.kf = None
+    p.fault = None
+    N = p.n_nodes
+    p.fixed = np.zeros((4, N), np.uint8)
+    p.fixed[0:3, : (p.nx + 1) * (p.ny + 1)] = 1
+    p.fixed[3, -3:] = 1
+    p.fu = np.zeros((3, N)); p.fp = np.zeros(N)
+    p.fp[N // 2] = 3e-5
+    p.fu[2, -1] = -1e5
+    p.dts = [1.0, 2.0, 4.0]
+    return p
+
+
+def setup(name, dt=1.7):
+    need_gpu()
+    prob = CASES[name]()
+    model = fem.Model(prob)
+    s = solver_for(prob)
+    s.timestep(dt)
+    return prob, model, s
+
+
+def lip_state(prob, model, s, seed):
+    """Seeded displacement with lip jumps; the fault state is evaluated on both sides."""
+    u = W.random_vectors(model.N, seed, scale_u=1e-5)[0]
+    if prob.kf is not None:
+        u += W.random_displacement_jump(prob, seed + 1, scale=5e-6)
+    st = osolve.initial_state(model)
+    r, force, Kcoh = osolve.fault_terms(model, u.reshape(-1), st.dlie)
+    g = s.fault_update(cuda(u)) if prob.kf is not None else None
+    return u, r, Kcoh, g
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_return_map(name):
+    prob, model, s = setup(name)
+    if prob.kf is None:
+        pytest.skip("no fault")
+    u, r, _, g = lip_state(prob, model, s, 11)
+    assert np.array_equal(g["flags"].cpu().numpy().astype(np.int64), r["state"])
+    assert len(set(r["state"].tolist())) >= 2          # the seeded jumps exercise several states
+    assert rel(g["tn"].cpu().numpy(), r["tn"]) < 1e-13
+    assert rel(g["ts"].cpu().numpy().T, r["ts"]) < 1e-13
+    assert rel(g["dlie"].cpu().numpy().T, r["dlie"]) < 1e-13
+    assert rel(g["T"].cpu().numpy().T, r["T"]) < 1e-12
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("op", ["KB", "KT", "A22", "APU", "AUP", "J"])
+def test_apply_fp64(name, op):
+    dt = 1.7
+    prob, model, s = setup(name, dt)
+    u, r, Kcoh, _ = lip_state(prob, model, s, 21)
+    x_u, x_p = W.random_vectors(model.N, 22)
+    if op == "KT" and prob.kf is None:
+        Kcoh = None
+        op_o = "Kb"
+    else:
+        op_o = {"KB": "Kb", "KT": "KT", "A22": "A22", "APU": "Apu", "AUP": "Aup", "J": "J"}[op]
+    yu_o, yp_o = osolve.apply(model, op_o, x_u.reshape(-1), x_p, dt=dt, Kcoh=Kcoh)
+    if op in ("KB", "KT"):
+        y = s.apply(op, cuda(x_u)).cpu().numpy()
+        assert rel(y.reshape(-1), yu_o) < 1e-12
+    elif op == "A22":
+        y = s.apply(op, cuda(x_p)).cpu().numpy()
+        assert rel(y, yp_o) < 1e-12
+    elif op == "APU":
+        y = s.apply(op, cuda(x_p)).cpu().numpy()
+        assert rel(y.reshape(-1), yu_o) < 1e-12
+    elif op == "AUP":
+        y = s.apply(op, cuda(x_u)).cpu().numpy()
+        assert rel(y, yp_o) < 1e-12
+    else:
+        x = np.concatenate([x_u, x_p[None]], axis=0)
+        y = s.apply(op, cuda(x)).cpu().numpy()
+        assert rel(y[:3].reshape(-1), yu_o) < 1e-12
+        assert rel(y[3], yp_o) < 1e-12
+
+
+@pytest.mark.parametrize("name", ["box_tied_8", "ragged_tied", "sheared_x_untied"])
+@pytest.mark.parametrize("op", ["KT", "A22", "J"])
+def test_apply_fp32(name, op):
+    dt = 1.7
+    prob, model, s = setup(name, dt)
+    u, r, Kcoh, _ = lip_state(prob, model, s, 31)
+    x_u, x_p = W.random_vectors(model.N, 32)
+    op_o = {"KT": "KT", "A22": "A22", "J": "J"}[op]
+    yu_o, yp_o = osolve.apply(model, op_o, x_u.reshape(-1), x_p, dt=dt, Kcoh=Kcoh)
+    if op == "KT":
+        y = s.apply(op, cuda(x_u, torch.float32)).cpu().numpy()
+        assert rel(y.reshape(-1), yu_o) < 2e-5
+    elif op == "A22":
+        y = s.apply(op, cuda(x_p, torch.float32)).cpu().numpy()
+        assert rel(y, yp_o) < 2e-5
+    else:
+        x = np.concatenate([x_u, x_p[None]], axis=0)
+        y = s.apply(op, cuda(x, torch.float32)).cpu().numpy()
+        assert rel(y[:3].reshape(-1), yu_o) < 2e-5
+
+
+@pytest.mark.parametrize("name", ["box_tied_8", "ragged_tied", "sheared_x_untied", "no_fault"])
+def test_residual(name):
+    dt = 1.3
+    prob, model, s = setup(name, dt)
+    du, dp = W.random_vectors(model.N, 41, scale_u=1e-6, scale_p=1e5)
+    # a state satisfies the homogeneous constraints: zero at constrained dofs
+    du = np.where(model.free_u.reshape(3, -1), du, 0.0)
+    dp = np.where(model.free_p, dp, 0.0)
+    st = osolve.initial_state(model)
+    _, force, _ = osolve.fault_terms(model, du.reshape(-1), st.dlie)
+    b1, b2 = osolve.residuals(model, st, du.reshape(-1), dp, dt, force)
+    rh = osolve.scaled_norm(model, b1, b2, model.A22(dt).diagonal())
+    b, rhat = s.residual(cuda(du), cuda(dp))
+    b = b.cpu().numpy()
+    assert rel(b[:3].reshape(-1), b1) < 1e-12
+    assert rel(b[3], b2) < 1e-12
+    assert abs(rhat - rh) <= 1e-12 * rh
+
+
+@pytest.mark.parametrize("name", ["box_tied_8", "sheared_x_untied", "no_fault"])
+@pytest.mark.parametrize("op", ["KT", "A22"])
+def test_pcg(name, op):
+    dt = 0.9
+    prob, model, s = setup(name, dt)
+    u, r, Kcoh, _ = lip_state(prob, model, s, 51)
+    if Kcoh is None or prob.kf is None:
+        Kcoh = model.Kb * 0
+    KT, Apu, A22 = osolve.jacobian_blocks(model, Kcoh, dt)
+    bu, bp = W.random_vectors(model.N, 52, scale_u=1e3, scale_p=1e-9)
+    from scipy.sparse.linalg import spsolve
+    if op == "KT":
+        b = np.where(model.free_u, bu.reshape(-1), 0.0)
+        x_o = np.zeros(3 * model.N)
+        x_o[model.free_u] = spsolve(KT.tocsc(), b[model.free_u])
+        x, rep = s.pcg("KT", cuda(b.reshape(3, -1)), rtol=1e-13, maxit=20000)
+        assert rel(x.cpu().numpy().reshape(-1), x_o) < 1e-9
+    else:
+        b = np.where(model.free_p, bp, 0.0)
+        x_o = np.zeros(model.N)
+        x_o[model.free_p] = spsolve(A22.tocsc(), b[model.free_p])
+        x, rep = s.pcg("A22", cuda(b), rtol=1e-13, maxit=20000)
+        assert rel(x.cpu().numpy(), x_o) < 1e-9
+    assert rep["iterations"] > 0 and rep["rel_residual"] <= 1e-13
+
+
+@pytest.mark.parametrize("name", ["box_tied_8", "sheared_x_untied", "chunk_at_upper_lip"])
+def test_prevost_vs_direct(name):
+    dt = 2.0
+    prob, model, s = setup(name, dt)
+    u, r, Kcoh, _ = lip_state(prob, model, s, 61)
+    KT, Apu, A22 = osolve.jacobian_blocks(model, Kcoh, dt)
+    bu, bp = W.random_vectors(model.N, 62, scale_u=1e3, scale_p=1e-9)
+    b1 = np.where(model.free_u, bu.reshape(-1), 0.0)
+    b2 = np.where(model.free_p, bp, 0.0)
+    x1, x2 = osolve.solve_monolithic(KT, Apu, A22, b1[model.free_u], b2[model.free_p], dense=False)
+    b = np.concatenate([b1.reshape(3, -1), b2[None]], axis=0)
+    x, rep = s.prevost(cuda(b), outer_rtol=1e-12, inner_rtol=1e-14)
+    x = x.cpu().numpy()
+    assert rel(x[:3].reshape(-1)[model.free_u], x1) < 1e-8
+    assert rel(x[3][model.free_p], x2) < 1e-8
+    assert rep["iterations"] >= 1
+
+
+@pytest.mark.parametrize("name,steps", [("box_tied_8", 5), ("sheared_x_untied", 2),
+                                        ("ragged_tied", 2), ("no_fault", 3)])
+def test_implicit_steps(name, steps):
+    prob = CASES[name]()
+    if name == "ragged_tied":
+        prob.fp = prob.fp * 20
+    need_gpu()
+    s = solver_for(prob)
+    model, ref = osolve.run(prob, nsteps=steps, rtol=1e-12)
+    for k in range(steps):
+        rep = s.step(prob.dts[k], newton_rtol=1e-12)
+        st = s.get_state()
+        r = ref[k]
+        assert rel(st["u"], r.u) < 1e-9, (k, rel(st["u"], r.u))
+        assert rel(st["p"], r.p) < 1e-9, (k, rel(st["p"], r.p))
+        if prob.kf is not None:
+            assert np.array_equal(st["flags"].astype(np.int64), r.flags), k
+            assert rel(st["slip"].T, r.slip) < 1e-9
+            assert rel(st["dlie"].T, r.dlie) < 1e-9 or np.abs(r.dlie).max() == 0
+    if name == "box_tied_8":
+        fl = st["flags"]
+        assert (fl == 0).sum() >= 1 and (fl == 2).sum() >= 4 and (fl == 1).sum() >= 4
+
+
+def test_state_roundtrip():
+    need_gpu()
+    prob = W.fault_small(steps=1)
+    s = solver_for(prob)
+    s.step(prob.dts[0])
+    a = s.get_state()
+    s2 = solver_for(prob)
+    s2.set_state(u=a["u"], p=a["p"], dlie=a["dlie"], flags=a["flags"])
+    b = s2.get_state()
+    for k in ("u", "p", "dlie", "flags", "slip"):
+        assert np.array_equal(a[k], b[k]), k
