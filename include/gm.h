@@ -227,6 +227,10 @@ int gm_state_device(gm_ctx* ctx, double** u_dev, double** p_dev);
 /* Number of nodes, elements and fault pairs of the bound problem. */
 int gm_sizes(const gm_ctx* ctx, int64_t* n_nodes, int64_t* n_el, int64_t* n_pairs);
 
+/* Counters since gm_assemble_or_bind: kernels launched by the library and bulk
+ * operator applications (any may be NULL). */
+int gm_counters(const gm_ctx* ctx, int64_t* kernel_launches, int64_t* bulk_applies);
+
 #ifdef __cplusplus
 }
 #endif

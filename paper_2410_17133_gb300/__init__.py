@@ -83,6 +83,7 @@ _SIG = {
     "gm_set_state": (C.c_int, [_P, _D, _D, _D, C.POINTER(C.c_int8)]),
     "gm_state_device": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P)]),
     "gm_sizes": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "gm_counters": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
 }
 
 _lib = None
@@ -300,6 +301,12 @@ class Solver:
                                        None if b is None else _dptr(b),
                                        None if d is None else _dptr(d),
                                        None if f is None else f.ctypes.data_as(C.POINTER(C.c_int8))))
+
+    def counters(self):
+        """(kernel launches, bulk operator applies) since bind."""
+        a, b = C.c_int64(), C.c_int64()
+        self._chk(self._L.gm_counters(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def state_device(self):
         """(u_ptr, p_ptr) raw device pointers of the accepted state."""

@@ -149,6 +149,7 @@ static void gm_apply_launch_t(gm_ctx* c, const RefOps<T>& R, double cK, double c
     constexpr int BULK = MODE & (GM_M_K | GM_M_APU | GM_M_AUP | GM_M_S | GM_M_C);
     gm_bulk_apply_kernel<T, CLS, BULK><<<dim3(gx, gy, gz), 256, 0, s>>>(b, R);
     c->applies++;
+    c->launches++;
     if (c->g.kf >= 0) {
         FaultArgs<T> f;
         f.g = c->g;
@@ -169,6 +170,7 @@ static void gm_apply_launch_t(gm_ctx* c, const RefOps<T>& R, double cK, double c
         f.skip = skip;
         const int nblk = (int)((c->g.nb + 255) / 256);
         gm_fault_apply_kernel<T, MODE><<<nblk, 256, 0, s>>>(f);
+        c->launches++;
     }
 }
 

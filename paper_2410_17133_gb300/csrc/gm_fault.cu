@@ -179,7 +179,7 @@ int gm_launch_return_map(gm_ctx* c, const double* un, const double* du, cudaStre
     a.D32 = c->dD32.as<float>();
     const int nblk = (int)((c->P + 255) / 256);
     gm_return_map_kernel<<<nblk, 256, 0, s>>>(a);
-    GM_CUDA_TRY(c, cudaGetLastError());
+    GM_LAUNCHED(c);
     return GM_OK;
 }
 
@@ -280,7 +280,7 @@ int gm_launch_residual(gm_ctx* c, const double* y1u, const double* y1p, const do
     a.counter = c->dcount.as<unsigned>();
     a.out = out2;
     gm_residual_kernel<<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(a);
-    GM_CUDA_TRY(c, cudaGetLastError());
+    GM_LAUNCHED(c);
     return GM_OK;
 }
 
@@ -390,7 +390,7 @@ int gm_launch_diag(gm_ctx* c, cudaStream_t s)
     a.Ainv32 = c->dAinv32.as<float>();
     const int nblk = (int)((c->N + 255) / 256);
     gm_diag_kernel<<<nblk, 256, 0, s>>>(a);
-    GM_CUDA_TRY(c, cudaGetLastError());
+    GM_LAUNCHED(c);
     return GM_OK;
 }
 
@@ -460,7 +460,7 @@ int gm_launch_block_jacobi(gm_ctx* c, cudaStream_t s)
     a.inv32 = c->dKinv32.as<float>();
     const int nblk = (int)((c->N + 255) / 256);
     gm_block_jacobi_kernel<<<nblk, 256, 0, s>>>(a);
-    GM_CUDA_TRY(c, cudaGetLastError());
+    GM_LAUNCHED(c);
     return GM_OK;
 }
 
@@ -480,6 +480,6 @@ int gm_launch_count_changes(gm_ctx* c, const int8_t* a, const int8_t* b, int* ou
     GM_CUDA_TRY(c, cudaMemsetAsync(out, 0, sizeof(int), s));
     if (c->P == 0) return GM_OK;
     gm_count_changes_kernel<<<64, 256, 0, s>>>(a, b, c->P, out);
-    GM_CUDA_TRY(c, cudaGetLastError());
+    GM_LAUNCHED(c);
     return GM_OK;
 }

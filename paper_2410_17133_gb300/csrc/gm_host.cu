@@ -385,6 +385,14 @@ int gm_sizes(const gm_ctx* c, int64_t* nn, int64_t* ne, int64_t* np)
     return GM_OK;
 }
 
+int gm_counters(const gm_ctx* c, int64_t* launches, int64_t* applies)
+{
+    if (!c) return GM_EINVAL;
+    if (launches) *launches = c->launches;
+    if (applies) *applies = c->applies;
+    return GM_OK;
+}
+
 int gm_apply_operator(gm_ctx* c, int which, const void* x, void* y, int dtype, void* stream)
 {
     if (!c) return GM_EINVAL;
@@ -867,6 +875,7 @@ int bind_impl(gm_ctx* c)
         }
     }
     c->applies = 0;
+    c->launches = 0;
     return GM_OK;
 }
 

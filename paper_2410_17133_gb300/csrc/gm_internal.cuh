@@ -242,12 +242,22 @@ struct gm_ctx {
     DevBuf dprevstate;
     void* hpin = nullptr;                              // pinned host scratch (4 KB)
     long long applies = 0;                             // bulk apply launches
+    long long launches = 0;                            // all kernel launches
 
     int set_err(int code, const std::string& msg) {
         err = msg;
         return code;
     }
 };
+
+// Count one kernel launch and check it.
+#define GM_LAUNCHED(ctx)                                                              \
+    do {                                                                              \
+        (ctx)->launches++;                                                            \
+        cudaError_t _e = cudaGetLastError();                                          \
+        if (_e != cudaSuccess)                                                        \
+            return (ctx)->set_err(GM_ECUDA, std::string("launch: ") + cudaGetErrorString(_e)); \
+    } while (0)
 
 #define GM_CUDA_TRY(ctx, call)                                                        \
     do {                                                                              \

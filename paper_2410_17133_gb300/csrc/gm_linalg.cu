@@ -65,16 +65,17 @@ __device__ bool gm_grid_sum_l(double (&v)[NV], double* part, unsigned* counter)
     return threadIdx.x == 0;
 }
 
-// Preconditioner application for one node.  WHICH 0: 3 components, 3x3
-// symmetric block inverse (6 per node);  WHICH 1: 1 component, diagonal inverse.
+// Preconditioner application for one node, in the vector precision T.
+// WHICH 0: 3 components, 3x3 symmetric block inverse (6 per node);
+// WHICH 1: 1 component, diagonal inverse.
 template <typename T, int WHICH>
 struct Prec;
 template <typename T>
 struct Prec<T, 0> {
     static constexpr int NC = 3;
-    __device__ static void apply(const T* mi, long long N, long long n, const double (&r)[3], double (&z)[3]) {
-        const double i0 = mi[n], i1 = mi[N + n], i2 = mi[2 * N + n];
-        const double i3 = mi[3 * N + n], i4 = mi[4 * N + n], i5 = mi[5 * N + n];
+    __device__ static void apply(const T* mi, long long N, long long n, const T (&r)[3], T (&z)[3]) {
+        const T i0 = mi[n], i1 = mi[N + n], i2 = mi[2 * N + n];
+        const T i3 = mi[3 * N + n], i4 = mi[4 * N + n], i5 = mi[5 * N + n];
         z[0] = i0 * r[0] + i1 * r[1] + i2 * r[2];
         z[1] = i1 * r[0] + i3 * r[1] + i4 * r[2];
         z[2] = i2 * r[0] + i4 * r[1] + i5 * r[2];
@@ -83,8 +84,8 @@ struct Prec<T, 0> {
 template <typename T>
 struct Prec<T, 1> {
     static constexpr int NC = 1;
-    __device__ static void apply(const T* mi, long long, long long n, const double (&r)[1], double (&z)[1]) {
-        z[0] = (double)mi[n] * r[0];
+    __device__ static void apply(const T* mi, long long, long long n, const T (&r)[1], T (&z)[1]) {
+        z[0] = mi[n] * r[0];
     }
 };
 
@@ -102,21 +103,18 @@ gm_pcg_init_kernel(long long N, const T* b, const T* q, T* r, T* z, T* p, const 
     double v[2] = {0.0, 0.0};
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
-        double rr[NC], zz[NC];
+        T rr[NC], zz[NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const double bq = (double)b[c * N + n] - (q ? (double)q[c * N + n] : 0.0);
-            rr[c] = (double)(T)bq;
-        }
+        for (int c = 0; c < NC; ++c) rr[c] = q ? b[c * N + n] - q[c * N + n] : b[c * N + n];
         Prec<T, WHICH>::apply(mi, N, n, rr, zz);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            const T zt = (T)zz[c];
-            r[c * N + n] = (T)rr[c];
-            z[c * N + n] = zt;
-            p[c * N + n] = zt;
-            v[0] += rr[c] * (double)zt;
-            v[1] += rr[c] * rr[c];
+            r[c * N + n] = rr[c];
+            z[c * N + n] = zz[c];
+            p[c * N + n] = zz[c];
+            // products of T values are exact in double; the sums accumulate in FP64
+            v[0] += (double)rr[c] * (double)zz[c];
+            v[1] += (double)rr[c] * (double)rr[c];
         }
     }
     if (gm_grid_sum_l<2>(v, rc.part, rc.counter)) {
@@ -162,26 +160,24 @@ gm_pcg_update_kernel(long long N, T* x, T* r, T* z, const T* p, const T* q, cons
 {
     constexpr int NC = Prec<T, WHICH>::NC;
     if (sc->done) return;
-    const double alpha = sc->alpha;
+    const T alpha = (T)sc->alpha;
     double v[2] = {0.0, 0.0};
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
-        double rr[NC], zz[NC];
+        T rr[NC], zz[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             const long long k = c * N + n;
-            const double pk = (double)p[k];
-            x[k] = (T)((double)x[k] + alpha * pk);
-            rr[c] = (double)(T)((double)r[k] - alpha * (double)q[k]);
-            r[k] = (T)rr[c];
+            x[k] = fma(alpha, p[k], x[k]);
+            rr[c] = fma(-alpha, q[k], r[k]);
+            r[k] = rr[c];
         }
         Prec<T, WHICH>::apply(mi, N, n, rr, zz);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            const T zt = (T)zz[c];
-            z[c * N + n] = zt;
-            v[0] += rr[c] * (double)zt;
-            v[1] += rr[c] * rr[c];
+            z[c * N + n] = zz[c];
+            v[0] += (double)rr[c] * (double)zz[c];
+            v[1] += (double)rr[c] * (double)rr[c];
         }
     }
     if (gm_grid_sum_l<2>(v, rc.part, rc.counter)) {
@@ -208,13 +204,13 @@ gm_pcg_dir_kernel(long long N, T* p, const T* z, const PcgScalars* sc)
 {
     constexpr int NC = Prec<T, WHICH>::NC;
     if (sc->done) return;
-    const double beta = sc->beta;
+    const T beta = (T)sc->beta;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x)
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             const long long k = c * N + n;
-            p[k] = (T)((double)z[k] + beta * (double)p[k]);
+            p[k] = fma(beta, p[k], z[k]);
         }
 }
 
@@ -266,7 +262,7 @@ int gm_launch_pcg_init(gm_ctx* c, int which, int prec, const void* b, const void
                 N, (const float*)b, (const float*)q, (float*)r, (float*)z, (float*)p,
                 prec_ptr<float>(c, 1), rtol, sc, rc);
     }
-    GM_CUDA_TRY(c, cudaGetLastError());
+    GM_LAUNCHED(c);
     return GM_OK;
 }
 
@@ -282,7 +278,7 @@ int gm_launch_pcg_alpha(gm_ctx* c, int which, int prec, const void* p, const voi
         if (which == 0) gm_pcg_alpha_kernel<float, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (const float*)p, (const float*)q, sc, rc);
         else gm_pcg_alpha_kernel<float, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (const float*)p, (const float*)q, sc, rc);
     }
-    GM_CUDA_TRY(c, cudaGetLastError());
+    GM_LAUNCHED(c);
     return GM_OK;
 }
 
@@ -310,7 +306,7 @@ int gm_launch_pcg_update(gm_ctx* c, int which, int prec, void* x, void* r, void*
                 N, (float*)x, (float*)r, (float*)z, (const float*)p, (const float*)q,
                 prec_ptr<float>(c, 1), sc, maxit, rc);
     }
-    GM_CUDA_TRY(c, cudaGetLastError());
+    GM_LAUNCHED(c);
     return GM_OK;
 }
 
@@ -325,7 +321,7 @@ int gm_launch_pcg_dir(gm_ctx* c, int which, int prec, void* p, const void* z, Pc
         if (which == 0) gm_pcg_dir_kernel<float, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (float*)p, (const float*)z, sc);
         else gm_pcg_dir_kernel<float, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (float*)p, (const float*)z, sc);
     }
-    GM_CUDA_TRY(c, cudaGetLastError());
+    GM_LAUNCHED(c);
     return GM_OK;
 }
 
@@ -343,7 +339,7 @@ int gm_launch_axpby(gm_ctx* c, long long n, double a, const double* x, double b,
                     cudaStream_t s)
 {
     gm_axpby_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(n, a, x, b, y);
-    GM_CUDA_TRY(c, cudaGetLastError());
+    GM_LAUNCHED(c);
     return GM_OK;
 }
 
@@ -369,19 +365,19 @@ __global__ void gm_axpy_f2d_kernel(long long n, double a, const float* x, double
 int gm_launch_copy_cast_d2f(gm_ctx* c, long long n, const double* x, float* y, cudaStream_t s)
 {
     gm_d2f_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(n, x, y);
-    GM_CUDA_TRY(c, cudaGetLastError());
+    GM_LAUNCHED(c);
     return GM_OK;
 }
 int gm_launch_copy_cast_f2d(gm_ctx* c, long long n, const float* x, double* y, cudaStream_t s)
 {
     gm_f2d_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(n, x, y);
-    GM_CUDA_TRY(c, cudaGetLastError());
+    GM_LAUNCHED(c);
     return GM_OK;
 }
 int gm_launch_axpy_f2d(gm_ctx* c, long long n, double a, const float* x, double* y, cudaStream_t s)
 {
     gm_axpy_f2d_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(n, a, x, y);
-    GM_CUDA_TRY(c, cudaGetLastError());
+    GM_LAUNCHED(c);
     return GM_OK;
 }
 
@@ -405,7 +401,7 @@ int gm_launch_dot(gm_ctx* c, long long n, const double* x, const double* y, cons
                   const double* y2, double* out, cudaStream_t s)
 {
     gm_dot_kernel<<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(n, x, y, x2, y2, out, redctx(c));
-    GM_CUDA_TRY(c, cudaGetLastError());
+    GM_LAUNCHED(c);
     return GM_OK;
 }
 
@@ -431,6 +427,6 @@ int gm_launch_jacobi_apply(gm_ctx* c, int which, const double* r, double* z, cud
         gm_jacobi_apply_kernel<0><<<GM_RED_BLOCKS, 256, 0, s>>>(c->N, c->dKinv64.as<double>(), r, z);
     else
         gm_jacobi_apply_kernel<1><<<GM_RED_BLOCKS, 256, 0, s>>>(c->N, c->dAinv64.as<double>(), r, z);
-    GM_CUDA_TRY(c, cudaGetLastError());
+    GM_LAUNCHED(c);
     return GM_OK;
 }
