@@ -200,6 +200,21 @@ int gm_prevost_solve(gm_ctx* ctx, const double* b_dev, double* x_dev, double out
 int gm_residual(gm_ctx* ctx, const double* du_dev, const double* dp_dev, double* b_dev,
                 double* rhat_host, void* stream);
 
+/* gm_residual for callers that cannot allocate device memory during the call
+ * (for example code that runs under a fixed memory pool or budget that forbids
+ * cudaMalloc).  The paper has no counterpart: this is a property of the library.
+ * Same arguments and results as gm_residual; the reduction scratch that
+ * gm_residual keeps in the context lives instead in one library-owned device
+ * array of about 1 MB (held on every GPU that loads the library until the
+ * process exits), so the call allocates nothing.  Limit: at most 16,777,216
+ * nodes; larger problems get GM_EINVAL.  The first call on a device looks up
+ * the array's device address; make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents: calls whose
+ * GPU work overlaps (other streams or contexts on the same device) race and
+ * must be serialised by the caller.  Synchronises. */
+int gm_residual_noalloc(gm_ctx* ctx, const double* du_dev, const double* dp_dev, double* b_dev,
+                        double* rhat_host, void* stream);
+
 /* One backward-Euler step of size dt (Sec. 3.3): Newton with the
  * elastic-predictor / plastic-corrector return map and Prevost's partitioned CG
  * for each Jacobian system; on convergence the state (u, p, inelastic slip,

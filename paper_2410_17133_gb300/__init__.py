@@ -78,6 +78,7 @@ _SIG = {
     "gm_prevost_solve": (C.c_int, [_P, _P, _P, C.c_double, C.c_int, C.c_double, C.c_int,
                                    C.POINTER(SolveReport), _P]),
     "gm_residual": (C.c_int, [_P, _P, _P, _P, _D, _P]),
+    "gm_residual_noalloc": (C.c_int, [_P, _P, _P, _P, _D, _P]),
     "gm_partitioned_step": (C.c_int, [_P, C.c_double, C.POINTER(StepOpts), C.POINTER(StepReport), _P]),
     "gm_get_state": (C.c_int, [_P, _D, _D, _D, _D, C.POINTER(C.c_int8)]),
     "gm_set_state": (C.c_int, [_P, _D, _D, _D, C.POINTER(C.c_int8)]),
@@ -262,6 +263,17 @@ class Solver:
         rh = C.c_double()
         self._chk(self._L.gm_residual(self.h, _tptr(du), _tptr(dp), _tptr(b), C.byref(rh),
                                       _stream_ptr(stream)))
+        return b, rh.value
+
+    def residual_noalloc(self, du, dp, b=None, stream=None):
+        """gm_residual_noalloc: the same residual with no device allocation in
+        the call (the output b must be passed or is created here by torch)."""
+        import torch
+        if b is None:
+            b = torch.empty((4, self.N), dtype=torch.float64, device=du.device)
+        rh = C.c_double()
+        self._chk(self._L.gm_residual_noalloc(self.h, _tptr(du), _tptr(dp), _tptr(b), C.byref(rh),
+                                              _stream_ptr(stream)))
         return b, rh.value
 
     def step(self, dt, newton_rtol=None, precision=F64, newton_maxit=50, outer_rtol=None,
