@@ -55,7 +55,38 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3,
                     help="steps of the plain FP64 solver timed beside the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--apply-profile", type=int, default=0, metavar="N",
+                    help="only run K_T applies (FP32 twice, FP64 twice) on the N^3 slip-front "
+                         "grid, for kernel profiling; prints their times")
     return ap.parse_args()
+
+
+def run_apply_profile(n):
+    """Small fixed sequence of bulk K_T applies (the dominant kernel) for ncu."""
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2410_17133_gb300 as gm
+    import workloads as W
+    prob = W.slip_front(n=n)
+    s = gm.Solver.from_problem(prob)
+    N = s.N
+    out = {"nodes": N, "elements": s.n_el}
+    for name, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+        x = (torch.randn(3, N, dtype=torch.float64, device="cuda") * 1e-6).to(dt)
+        y = torch.empty_like(x)
+        ms = []
+        for _ in range(2):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            s.apply("KT", x, y)
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        out[name + "_ms"] = ms
+    print(json.dumps(out))
 
 
 def workload(name):
@@ -400,6 +431,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.apply_profile:
+        run_apply_profile(args.apply_profile)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

@@ -1,4 +1,4 @@
-// Fault (interface) part of the operators and the apply launcher.
+// Fault (interface) part of the operators and the apply launchers.
 //
 // Per node pair i (lips i-, i+), nodal quadrature with weight A_i:
 //   cohesive tangent     y_u+- += +- cKf A_i D_i [[x_u]]                  (Sec. 3.3.1)
@@ -12,11 +12,43 @@
 // are distributed half/half to the two lips; with tied lips (k_perp infinite)
 // the single pressure lives on the lower lip and the upper-lip bulk row,
 // written raw by the bulk kernel, is folded into it here.
+//
+// In PCG mode this kernel is the last writer of the lip rows, so it also adds
+// p.(A p) over the lip nodes to the bulk kernel's per-CTA partials, and its last
+// block sums all partials in a fixed order and forms alpha = (r.z)/(p.Ap).
 #pragma once
 
 #include "gm_bulk.cuh"
 
-template <typename T, int MODE>
+__device__ inline void gm_pcg_alpha_from(PcgScalars* sc, double pq)
+{
+    sc->pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+        sc->status = isfinite(pq) ? GM_ENOCONV : GM_ENAN;
+        sc->done = 1;
+        sc->alpha = 0.0;
+    } else {
+        sc->alpha = sc->rz / pq;
+    }
+}
+
+// Sum n partials in a fixed order with one block (thread-strided, then a tree).
+__device__ inline double gm_block_sum_fixed(const double* part, int n)
+{
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) acc += ((volatile const double*)part)[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    double tot = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
+    return tot;
+}
+
+template <typename T, int MODE, bool PCG>
 __global__ void __launch_bounds__(256)
 gm_fault_apply_kernel(const FaultArgs<T> a)
 {
@@ -33,92 +65,204 @@ gm_fault_apply_kernel(const FaultArgs<T> a)
     const GridDesc& g = a.g;
     const long long P = g.nb;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P) return;
-    const int pi = (int)(i % (g.nx + 1)), pj = (int)(i / (g.nx + 1));
     const long long N = g.N;
-    const long long nm = i + g.nb * g.kf, np = nm + g.nb;
-    const unsigned mm = a.mask[nm], mp = a.mask[np];
-    const int nqi = (pi > 0) + (pi < g.nx), nqj = (pj > 0) + (pj < g.ny);
-    const T Ai = a.Aq * T(0.25) * T(nqi * nqj);
+    double dot = 0.0;
+    if (i < P) {
+        const int pi = (int)(i % (g.nx + 1)), pj = (int)(i / (g.nx + 1));
+        const long long nm = i + g.nb * g.kf, np = nm + g.nb;
+        const unsigned mm = a.mask[nm], mp = a.mask[np];
+        const int nqi = (pi > 0) + (pi < g.nx), nqj = (pj > 0) + (pj < g.ny);
+        const T Ai = a.Aq * T(0.25) * T(nqi * nqj);
 
-    auto pval = [&](long long node) -> T {   // masked pressure input
-        return ((a.mask[node] >> 3) & 1u) ? T(0) : a.xp[node];
-    };
-    // pressure of the mid-plane <p> at pair id q
-    auto pav = [&](long long q) -> T {
-        const long long m = q + g.nb * g.kf;
-        if (g.tied) return pval(m);
-        return T(0.5) * (pval(m) + pval(m + g.nb));
-    };
+        auto pval = [&](long long node) -> T {   // masked pressure input
+            return ((a.mask[node] >> 3) & 1u) ? T(0) : a.xp[node];
+        };
+        // pressure of the mid-plane <p> at pair id q
+        auto pav = [&](long long q) -> T {
+            const long long m = q + g.nb * g.kf;
+            if (g.tied) return pval(m);
+            return T(0.5) * (pval(m) + pval(m + g.nb));
+        };
 
-    T jmp[3] = {T(0), T(0), T(0)};
-    if constexpr (DO_KF || DO_AUP) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const T up = ((mp >> c) & 1u) ? T(0) : a.xu[c * N + np];
-            const T um = ((mm >> c) & 1u) ? T(0) : a.xu[c * N + nm];
-            jmp[c] = up - um;
-        }
-    }
-    T p_av = T(0);
-    if constexpr (DO_APU || DO_S) p_av = pav(i);
-
-    if constexpr (OUT_U) {
-        T f[3] = {T(0), T(0), T(0)};
-        if constexpr (DO_KF) {
-            const T d00 = a.D[i], d01 = a.D[P + i], d02 = a.D[2 * P + i];
-            const T d11 = a.D[3 * P + i], d12 = a.D[4 * P + i], d22 = a.D[5 * P + i];
-            const T s = a.cKf * Ai;
-            f[0] = s * (d00 * jmp[0] + d01 * jmp[1] + d02 * jmp[2]);
-            f[1] = s * (d01 * jmp[0] + d11 * jmp[1] + d12 * jmp[2]);
-            f[2] = s * (d02 * jmp[0] + d12 * jmp[1] + d22 * jmp[2]);
-        }
-        if constexpr (DO_APU) {
-            const T s = a.cApu * Ai * p_av;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) f[c] = fma(s, a.n[c], f[c]);
-        }
-        if constexpr (DO_KF || DO_APU) {
+        T jmp[3] = {T(0), T(0), T(0)};
+        if constexpr (DO_KF || DO_AUP) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                if (!((mp >> c) & 1u)) a.yu[c * N + np] += f[c];
-                if (!((mm >> c) & 1u)) a.yu[c * N + nm] -= f[c];
+                const T up = ((mp >> c) & 1u) ? T(0) : a.xu[c * N + np];
+                const T um = ((mm >> c) & 1u) ? T(0) : a.xu[c * N + nm];
+                jmp[c] = up - um;
+            }
+        }
+        T p_av = T(0);
+        if constexpr (DO_APU || DO_S) p_av = pav(i);
+
+        if constexpr (OUT_U) {
+            T f[3] = {T(0), T(0), T(0)};
+            if constexpr (DO_KF) {
+                const T d00 = a.D[i], d01 = a.D[P + i], d02 = a.D[2 * P + i];
+                const T d11 = a.D[3 * P + i], d12 = a.D[4 * P + i], d22 = a.D[5 * P + i];
+                const T s = a.cKf * Ai;
+                f[0] = s * (d00 * jmp[0] + d01 * jmp[1] + d02 * jmp[2]);
+                f[1] = s * (d01 * jmp[0] + d11 * jmp[1] + d12 * jmp[2]);
+                f[2] = s * (d02 * jmp[0] + d12 * jmp[1] + d22 * jmp[2]);
+            }
+            if constexpr (DO_APU) {
+                const T s = a.cApu * Ai * p_av;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) f[c] = fma(s, a.n[c], f[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (!((mp >> c) & 1u)) {
+                    const T y = a.yu[c * N + np] + f[c];
+                    a.yu[c * N + np] = y;
+                    if constexpr (PCG) dot += (double)a.xu[c * N + np] * (double)y;
+                }
+                if (!((mm >> c) & 1u)) {
+                    const T y = a.yu[c * N + nm] - f[c];
+                    a.yu[c * N + nm] = y;
+                    if constexpr (PCG) dot += (double)a.xu[c * N + nm] * (double)y;
+                }
+            }
+        }
+
+        if constexpr (OUT_P) {
+            T dav = T(0);    // contribution on the <p> test function
+            if constexpr (DO_AUP) dav = a.cAup * Ai * (a.n[0] * jmp[0] + a.n[1] * jmp[1] + a.n[2] * jmp[2]);
+            if constexpr (DO_S) dav = fma(a.cS * Ai * a.stor, p_av, dav);
+            T dtr = T(0);    // transverse contribution on [[p]]
+            if constexpr (DO_C) {
+                T lap = T(0);
+#pragma unroll
+                for (int dq = 0; dq < 4; ++dq) {
+                    const int qi = pi - 1 + (dq & 1), qj = pj - 1 + (dq >> 1);
+                    if (qi < 0 || qi >= g.nx || qj < 0 || qj >= g.ny) continue;
+                    const int b = (pi - qi) + 2 * (pj - qj);
+#pragma unroll
+                    for (int b2 = 0; b2 < 4; ++b2) {
+                        const long long q = (qi + (b2 & 1)) + (long long)(g.nx + 1) * (qj + (b2 >> 1));
+                        lap = fma(a.Lf[b * 4 + b2], pav(q), lap);
+                    }
+                }
+                dav = fma(a.cC * a.lcoef, lap, dav);
+                if (!g.tied) dtr = a.cC * Ai * a.tcoef * (pval(np) - pval(nm));
+            }
+            if (g.tied) {
+                T v = dav;
+                if constexpr (BULK_P) v += a.yp[nm] + a.yp[np];
+                const T y = ((mm >> 3) & 1u) ? T(0) : v;
+                a.yp[nm] = y;
+                a.yp[np] = T(0);
+                if constexpr (PCG) dot += (double)pval(nm) * (double)y;
+            } else {
+                const T vp = T(0.5) * dav + dtr, vm = T(0.5) * dav - dtr;
+                if (!((mp >> 3) & 1u)) {
+                    const T y = a.yp[np] + vp;
+                    a.yp[np] = y;
+                    if constexpr (PCG) dot += (double)a.xp[np] * (double)y;
+                }
+                if (!((mm >> 3) & 1u)) {
+                    const T y = a.yp[nm] + vm;
+                    a.yp[nm] = y;
+                    if constexpr (PCG) dot += (double)a.xp[nm] * (double)y;
+                }
             }
         }
     }
 
-    if constexpr (OUT_P) {
-        T dav = T(0);    // contribution on the <p> test function
-        if constexpr (DO_AUP) dav = a.cAup * Ai * (a.n[0] * jmp[0] + a.n[1] * jmp[1] + a.n[2] * jmp[2]);
-        if constexpr (DO_S) dav = fma(a.cS * Ai * a.stor, p_av, dav);
-        T dtr = T(0);    // transverse contribution on [[p]]
-        if constexpr (DO_C) {
-            T lap = T(0);
+    if constexpr (PCG) {
+        __shared__ double sh[8];
+        __shared__ bool last;
 #pragma unroll
-            for (int dq = 0; dq < 4; ++dq) {
-                const int qi = pi - 1 + (dq & 1), qj = pj - 1 + (dq >> 1);
-                if (qi < 0 || qi >= g.nx || qj < 0 || qj >= g.ny) continue;
-                const int b = (pi - qi) + 2 * (pj - qj);
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = dot;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
 #pragma unroll
-                for (int b2 = 0; b2 < 4; ++b2) {
-                    const long long q = (qi + (b2 & 1)) + (long long)(g.nx + 1) * (qj + (b2 >> 1));
-                    lap = fma(a.Lf[b * 4 + b2], pav(q), lap);
-                }
-            }
-            dav = fma(a.cC * a.lcoef, lap, dav);
-            if (!g.tied) dtr = a.cC * Ai * a.tcoef * (pval(np) - pval(nm));
+            for (int w = 0; w < 8; ++w) s += sh[w];
+            a.part[a.nbulk + blockIdx.x] = s;
+            __threadfence();
+            last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
         }
-        if (g.tied) {
-            T v = dav;
-            if constexpr (BULK_P) v += a.yp[nm] + a.yp[np];
-            a.yp[nm] = ((mm >> 3) & 1u) ? T(0) : v;
-            a.yp[np] = T(0);
-        } else {
-            const T vp = T(0.5) * dav + dtr, vm = T(0.5) * dav - dtr;
-            if (!((mp >> 3) & 1u)) a.yp[np] += vp;
-            if (!((mm >> 3) & 1u)) a.yp[nm] += vm;
+        __syncthreads();
+        if (!last) return;
+        __threadfence();
+        const double pq = gm_block_sum_fixed(a.part, a.nbulk + (int)gridDim.x);
+        if (threadIdx.x == 0) {
+            gm_pcg_alpha_from(a.sc, pq);
+            *a.counter = 0u;
         }
     }
+}
+
+// Without a fault, one block closes the p.Ap reduction of the bulk partials.
+static __global__ void __launch_bounds__(256)
+gm_pcg_alpha_finalize_kernel(const double* part, int n, PcgScalars* sc)
+{
+    if (sc->done) return;
+    const double pq = gm_block_sum_fixed(part, n);
+    if (threadIdx.x == 0) gm_pcg_alpha_from(sc, pq);
+}
+
+inline void gm_bulk_geometry(const gm_ctx* c, int* gx, int* gy, int* gz, int* zchunk)
+{
+    // chunk of node planes per CTA: aim for >= 4 CTAs per SM on the xy tiling
+    *gx = (c->nx + 1 + 14) / 15;
+    *gy = (c->ny + 1 + 14) / 15;
+    const long long xy = (long long)(*gx) * (*gy);
+    int nzc = (int)((4LL * c->sm_count + xy - 1) / xy);
+    if (nzc < 1) nzc = 1;
+    int zc = (c->g.nplanes + nzc - 1) / nzc;
+    if (zc < 4) zc = 4;
+    *zchunk = zc;
+    *gz = (c->g.nplanes + zc - 1) / zc;
+}
+
+template <typename T>
+inline FaultArgs<T> gm_fault_args(gm_ctx* c, double cK, double cApu, double cAup, double cS, double cC,
+                                  bool kf_on)
+{
+    FaultArgs<T> f;
+    f.g = c->g;
+    f.cKf = T(kf_on ? cK : 0.0);
+    f.cApu = T(cApu);
+    f.cAup = T(cAup);
+    f.cS = T(cS);
+    f.cC = T(cC);
+    f.Aq = T(c->Aq);
+    for (int d = 0; d < 3; ++d) f.n[d] = T(c->nrm[d]);
+    f.stor = T(c->fp.w0 / c->fp.MF);
+    f.lcoef = T(c->fp.wk_par / c->mu_f);
+    f.tcoef = T(c->fp.k_perp > 0 ? c->fp.k_perp / (c->mu_f * c->fp.w0) : 0.0);
+    for (int q = 0; q < 16; ++q) f.Lf[q] = T(c->Lf[q]);
+    f.mask = c->dmask.as<uint8_t>();
+    f.skip = nullptr;
+    f.part = nullptr;
+    f.nbulk = 0;
+    f.counter = nullptr;
+    f.sc = nullptr;
+    return f;
+}
+
+template <typename T>
+inline BulkArgs<T> gm_bulk_args(gm_ctx* c, double cK, double cApu, double cAup, double cS, double cC,
+                                const T* E, const T* kap)
+{
+    BulkArgs<T> b;
+    b.g = c->g;
+    b.E = E;
+    b.kap = kap;
+    b.mask = c->dmask.as<uint8_t>();
+    b.cK = T(cK);
+    b.cApu = T(cApu * c->alpha);
+    b.cAup = T(cAup * c->alpha);
+    b.cS = T(cS / c->M);
+    b.cC = T(cC);
+    b.skip = nullptr;
+    b.zu = nullptr; b.zp = nullptr; b.pu_new = nullptr; b.pp_new = nullptr;
+    b.beta = nullptr; b.part = nullptr;
+    return b;
 }
 
 template <typename T, int CLS, int MODE>
@@ -126,50 +270,23 @@ static void gm_apply_launch_t(gm_ctx* c, const RefOps<T>& R, double cK, double c
                               double cS, double cC, const T* xu, const T* xp, T* yu, T* yp,
                               const T* E, const T* kap, const T* D, cudaStream_t s, const int* skip)
 {
-    BulkArgs<T> b;
-    b.g = c->g;
-    // chunk of node planes per CTA: aim for >= 4 CTAs per SM on the xy tiling
-    const int gx = (c->nx + 1 + 14) / 15, gy = (c->ny + 1 + 14) / 15;
-    const long long xy = (long long)gx * gy;
-    int nzc = (int)((4LL * c->sm_count + xy - 1) / xy);
-    if (nzc < 1) nzc = 1;
-    int zchunk = (c->g.nplanes + nzc - 1) / nzc;
-    if (zchunk < 4) zchunk = 4;
-    const int gz = (c->g.nplanes + zchunk - 1) / zchunk;
+    int gx, gy, gz, zchunk;
+    gm_bulk_geometry(c, &gx, &gy, &gz, &zchunk);
+    BulkArgs<T> b = gm_bulk_args<T>(c, cK, cApu, cAup, cS, cC, E, kap);
     b.zchunk = zchunk;
     b.xu = xu; b.xp = xp; b.yu = yu; b.yp = yp;
-    b.E = E; b.kap = kap;
-    b.mask = c->dmask.as<uint8_t>();
-    b.cK = T(cK);
-    b.cApu = T(cApu * c->alpha);
-    b.cAup = T(cAup * c->alpha);
-    b.cS = T(cS / c->M);
-    b.cC = T(cC);
     b.skip = skip;
     constexpr int BULK = MODE & (GM_M_K | GM_M_APU | GM_M_AUP | GM_M_S | GM_M_C);
-    gm_bulk_apply_kernel<T, CLS, BULK><<<dim3(gx, gy, gz), 256, 0, s>>>(b, R);
+    gm_bulk_apply_kernel<T, CLS, BULK, false><<<dim3(gx, gy, gz), 256, 0, s>>>(b, R);
     c->applies++;
     c->launches++;
     if (c->g.kf >= 0) {
-        FaultArgs<T> f;
-        f.g = c->g;
+        FaultArgs<T> f = gm_fault_args<T>(c, cK, cApu, cAup, cS, cC, (MODE & GM_M_KF) != 0);
         f.xu = xu; f.xp = xp; f.yu = yu; f.yp = yp;
         f.D = D;
-        f.mask = c->dmask.as<uint8_t>();
-        f.cKf = T((MODE & GM_M_KF) ? cK : 0.0);
-        f.cApu = T(cApu);
-        f.cAup = T(cAup);
-        f.cS = T(cS);
-        f.cC = T(cC);
-        f.Aq = T(c->Aq);
-        for (int d = 0; d < 3; ++d) f.n[d] = T(c->nrm[d]);
-        f.stor = T(c->fp.w0 / c->fp.MF);
-        f.lcoef = T(c->fp.wk_par / c->mu_f);
-        f.tcoef = T(c->fp.k_perp > 0 ? c->fp.k_perp / (c->mu_f * c->fp.w0) : 0.0);
-        for (int q = 0; q < 16; ++q) f.Lf[q] = T(c->Lf[q]);
         f.skip = skip;
         const int nblk = (int)((c->g.nb + 255) / 256);
-        gm_fault_apply_kernel<T, MODE><<<nblk, 256, 0, s>>>(f);
+        gm_fault_apply_kernel<T, MODE, false><<<nblk, 256, 0, s>>>(f);
         c->launches++;
     }
 }
@@ -190,5 +307,58 @@ static void gm_apply_dispatch_cls(gm_ctx* c, const RefOps<T>& R, double cK, doub
     default:
         gm_apply_launch_t<T, GM_CLS_GEN, MODE>(c, R, cK, cApu, cAup, cS, cC, xu, xp, yu, yp, E, kap, D, s, skip);
         break;
+    }
+}
+
+// Fused PCG operator step for K_T (which 0) or A22 (which 1).
+template <typename T, int CLS, int MODE>
+static void gm_pcg_apply_t(gm_ctx* c, const RefOps<T>& R, const T* z, const T* p_old, T* p_new, T* q,
+                           const T* E, const T* kap, const T* D, PcgScalars* sc, cudaStream_t s)
+{
+    constexpr bool U = (MODE & GM_M_K) != 0;
+    const double cK = U ? 1.0 : 0.0, cS = U ? 0.0 : 1.0, cC = U ? 0.0 : c->dt;
+    int gx, gy, gz, zchunk;
+    gm_bulk_geometry(c, &gx, &gy, &gz, &zchunk);
+    const int nbulk = gx * gy * gz;
+    double* part = c->dpart.as<double>();
+    BulkArgs<T> b = gm_bulk_args<T>(c, cK, 0, 0, cS, cC, E, kap);
+    b.zchunk = zchunk;
+    b.skip = &sc->done;
+    b.beta = &sc->beta;
+    b.part = part;
+    if (U) { b.xu = p_old; b.zu = z; b.pu_new = p_new; b.yu = q; b.xp = nullptr; b.yp = nullptr; }
+    else { b.xp = p_old; b.zp = z; b.pp_new = p_new; b.yp = q; b.xu = nullptr; b.yu = nullptr; }
+    constexpr int BULK = MODE & (GM_M_K | GM_M_S | GM_M_C);
+    gm_bulk_apply_kernel<T, CLS, BULK, true><<<dim3(gx, gy, gz), 256, 0, s>>>(b, R);
+    c->applies++;
+    c->launches++;
+    if (c->g.kf >= 0) {
+        FaultArgs<T> f = gm_fault_args<T>(c, cK, 0, 0, cS, cC, U);
+        if (U) { f.xu = p_new; f.yu = q; f.xp = nullptr; f.yp = nullptr; }
+        else { f.xp = p_new; f.yp = q; f.xu = nullptr; f.yu = nullptr; }
+        f.D = D;
+        f.skip = &sc->done;
+        f.part = part;
+        f.nbulk = nbulk;
+        f.counter = c->dcount.as<unsigned>();
+        f.sc = sc;
+        const int nblk = (int)((c->g.nb + 255) / 256);
+        gm_fault_apply_kernel<T, MODE, true><<<nblk, 256, 0, s>>>(f);
+        c->launches++;
+    } else {
+        gm_pcg_alpha_finalize_kernel<<<1, 256, 0, s>>>(part, nbulk, sc);
+        c->launches++;
+    }
+}
+
+template <typename T, int MODE>
+static void gm_pcg_apply_dispatch(gm_ctx* c, const RefOps<T>& R, const T* z, const T* p_old, T* p_new,
+                                  T* q, const T* E, const T* kap, const T* D, PcgScalars* sc,
+                                  cudaStream_t s)
+{
+    switch (c->cls) {
+    case GM_CLS_BOX: gm_pcg_apply_t<T, GM_CLS_BOX, MODE>(c, R, z, p_old, p_new, q, E, kap, D, sc, s); break;
+    case GM_CLS_MONO: gm_pcg_apply_t<T, GM_CLS_MONO, MODE>(c, R, z, p_old, p_new, q, E, kap, D, sc, s); break;
+    default: gm_pcg_apply_t<T, GM_CLS_GEN, MODE>(c, R, z, p_old, p_new, q, E, kap, D, sc, s); break;
     }
 }

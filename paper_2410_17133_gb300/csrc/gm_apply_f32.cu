@@ -27,3 +27,18 @@ int gm_launch_apply_f32(gm_ctx* c, int mode, double cK, double cApu, double cAup
     if (e != cudaSuccess) return c->set_err(GM_ECUDA, std::string("apply launch: ") + cudaGetErrorString(e));
     return GM_OK;
 }
+
+int gm_launch_pcg_apply_f32(gm_ctx* c, int which, const float* z, const float* p_old, float* p_new, float* q,
+                            PcgScalars* sc, cudaStream_t s)
+{
+    const float* E = c->dE32.as<float>();
+    const float* kap = c->dK32.as<float>();
+    const float* D = c->dD32.as<float>();
+    if (which == 0)
+        gm_pcg_apply_dispatch<float, GM_MODE_KT>(c, c->R32, z, p_old, p_new, q, E, kap, D, sc, s);
+    else
+        gm_pcg_apply_dispatch<float, GM_MODE_A22>(c, c->R32, z, p_old, p_new, q, E, kap, D, sc, s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return c->set_err(GM_ECUDA, std::string("pcg apply launch: ") + cudaGetErrorString(e));
+    return GM_OK;
+}

@@ -28,3 +28,18 @@ int gm_launch_apply_f64(gm_ctx* c, int mode, double cK, double cApu, double cAup
     if (e != cudaSuccess) return c->set_err(GM_ECUDA, std::string("apply launch: ") + cudaGetErrorString(e));
     return GM_OK;
 }
+
+int gm_launch_pcg_apply_f64(gm_ctx* c, int which, const double* z, const double* p_old, double* p_new, double* q,
+                            PcgScalars* sc, cudaStream_t s)
+{
+    const double* E = c->dE64.as<double>();
+    const double* kap = c->dK64.as<double>();
+    const double* D = c->dD64.as<double>();
+    if (which == 0)
+        gm_pcg_apply_dispatch<double, GM_MODE_KT>(c, c->R64, z, p_old, p_new, q, E, kap, D, sc, s);
+    else
+        gm_pcg_apply_dispatch<double, GM_MODE_A22>(c, c->R64, z, p_old, p_new, q, E, kap, D, sc, s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return c->set_err(GM_ECUDA, std::string("pcg apply launch: ") + cudaGetErrorString(e));
+    return GM_OK;
+}

@@ -14,18 +14,38 @@
 // Work decomposition: a CTA of 16x16 threads owns 15x15 node columns and a
 // chunk of node planes; it marches up the planes.  Thread (tx, ty) handles the
 // element column (face) whose lower-left node is tile node (tx, ty), so each
-// element is computed exactly once inside the CTA, plus one halo column/row and
-// one halo layer that are recomputed by the neighbour.  The transform is split:
-// the xy part is done once per node plane per face and reused by the element
-// layers below and above the plane; the z part per element.  Element results
-// are accumulated per face in registers across the plane, then each node sums
-// its four faces from shared memory.  No atomics; results are deterministic.
+// element is computed once inside the CTA, plus one halo column/row and one halo
+// layer that the neighbour also computes.  The transform is split: the xy part
+// is done once per node plane per face and reused by the element layers below
+// and above the plane; the z part per element.  Element results are accumulated
+// per face in registers across the plane, then each node sums its four faces
+// from shared memory.  No atomics; results are deterministic.
+//
+// Pipelining: the node plane two levels up is fetched from global memory into
+// registers while the current element layer is computed, and stored to the
+// second of two shared plane buffers afterwards, so each plane step has two
+// barriers and its global-load latency overlaps the arithmetic.
+//
+// PCG mode (inner solves, one field group): the input is the new search
+// direction p = z + beta p_old formed while loading; the owner of each node
+// writes p to a second buffer (p is double-buffered across iterations because
+// neighbouring CTAs read p_old as halo), and the kernel leaves a per-CTA
+// partial of p . (A p) over the nodes that are not on a fault lip.
 #pragma once
 
 #include "gm_internal.cuh"
 
+// Resident CTAs per SM the register allocation must allow: FP64 is bound by
+// the FP64 pipe at one CTA; the FP32 single-field-group box kernels fit three.
 template <typename T, int CLS, int MODE>
-__global__ void __launch_bounds__(256)
+constexpr int gm_bulk_min_blocks()
+{
+    return sizeof(T) == 8 ? 1
+         : (CLS == GM_CLS_BOX && (MODE == GM_M_K || MODE == (GM_M_S | GM_M_C))) ? 3 : 2;
+}
+
+template <typename T, int CLS, int MODE, bool PCG>
+__global__ void __launch_bounds__(256, gm_bulk_min_blocks<T, CLS, MODE>())
 gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
 {
     constexpr bool DO_K = (MODE & GM_M_K) != 0;
@@ -43,10 +63,11 @@ gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
     constexpr int OPI = OUT_U ? 3 : 0;  // slot of p among the output fields
     constexpr SecTab ST = gm_make_sectab(CLS);
     constexpr int NB = ST.nb, BU = ST.bu, BP = ST.bp;
+    static_assert(!PCG || (NI == NO && (NI == 3 || NI == 1)), "PCG mode needs a square single-field-group operator");
 
     if (a.skip != nullptr && *a.skip != 0) return;
 
-    __shared__ T s_plane[NI][17 * 17];
+    __shared__ T s_plane[2][NI][17 * 17];
     __shared__ T s_face[NO][4][256];
 
     const GridDesc& g = a.g;
@@ -59,44 +80,71 @@ gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
     const int z1 = min(z0 + a.zchunk, g.nplanes);
     const long long N = g.N;
     const long long rowlen = g.nx + 1;
+    T beta = T(0);
+    if constexpr (PCG) beta = (T)(*a.beta);
 
-    // element layer between extended planes kb and kb+1 exists?
     auto layer_exists = [&](int kb) -> bool {
         return kb >= 0 && kb + 1 < g.nplanes && kb != g.kf;
     };
     auto layer_index = [&](int kb) -> int { return (g.kf >= 0 && kb > g.kf) ? kb - 1 : kb; };
 
-    auto load_plane = [&](int kk) {
-        for (int idx = tid; idx < 17 * 17; idx += 256) {
+    // input value of field f at a node (masked; PCG mode forms z + beta p_old)
+    auto in_u = [&](int c, long long node) -> T {
+        if constexpr (PCG) return a.zu[c * N + node] + beta * a.xu[c * N + node];
+        else return a.xu[c * N + node];
+    };
+    auto in_p = [&](long long node) -> T {
+        if constexpr (PCG) return a.zp[node] + beta * a.xp[node];
+        else return a.xp[node];
+    };
+
+    // fetch one node plane (tile + halo) into registers: slots tid and tid + 256
+    T pf[2][NI];
+    auto fetch = [&](int kk) {
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl) {
+            const int idx = tid + sl * 256;
+#pragma unroll
+            for (int f = 0; f < NI; ++f) pf[sl][f] = T(0);
+            if (idx >= 17 * 17) continue;
             const int ni = idx % 17, nj = idx / 17;
             const int gi = x0 - 1 + ni, gj = y0 - 1 + nj;
-            const bool ok = gi >= 0 && gi <= g.nx && gj >= 0 && gj <= g.ny;
-            const long long node = ok ? (gi + rowlen * (gj + (long long)(g.ny + 1) * kk)) : 0;
-            const unsigned m = ok ? a.mask[node] : 0xFu;
+            if (gi < 0 || gi > g.nx || gj < 0 || gj > g.ny) continue;
+            const long long node = gi + rowlen * (gj + (long long)(g.ny + 1) * kk);
+            const unsigned m = a.mask[node];
             if constexpr (IN_U) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
-                    s_plane[c][idx] = ((m >> c) & 1u) ? T(0) : a.xu[c * N + node];
+                    if (!((m >> c) & 1u)) pf[sl][c] = in_u(c, node);
             }
             if constexpr (IN_P) {
                 long long pn = node;
                 unsigned pm = m;
-                if (ok && g.tied && kk == g.kf + 1) {   // slave lip reads its master
+                if (g.tied && kk == g.kf + 1) {   // slave lip reads its master
                     pn = node - g.nb;
                     pm = a.mask[pn];
                 }
-                s_plane[IPI][idx] = ((pm >> 3) & 1u) ? T(0) : a.xp[pn];
+                if (!((pm >> 3) & 1u)) pf[sl][IPI] = in_p(pn);
             }
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl) {
+            const int idx = tid + sl * 256;
+            if (idx < 17 * 17)
+#pragma unroll
+                for (int f = 0; f < NI; ++f) s_plane[buf][f][idx] = pf[sl][f];
         }
     };
 
     // xy part of the forward transform for this thread's face:
     // t[sx + 2 sy] = sum_{ax,ay} (-1)^(sx ax + sy ay) v[ax, ay]
-    auto fwd_xy = [&](T (&t)[NI][4]) {
+    auto fwd_xy = [&](int buf, T (&t)[NI][4]) {
 #pragma unroll
         for (int f = 0; f < NI; ++f) {
-            const T v00 = s_plane[f][ty * 17 + tx], v10 = s_plane[f][ty * 17 + tx + 1];
-            const T v01 = s_plane[f][(ty + 1) * 17 + tx], v11 = s_plane[f][(ty + 1) * 17 + tx + 1];
+            const T v00 = s_plane[buf][f][ty * 17 + tx], v10 = s_plane[buf][f][ty * 17 + tx + 1];
+            const T v01 = s_plane[buf][f][(ty + 1) * 17 + tx], v11 = s_plane[buf][f][(ty + 1) * 17 + tx + 1];
             const T a0 = v00 + v10, a1 = v00 - v10, b0 = v01 + v11, b1 = v01 - v11;
             t[f][0] = a0 + b0;
             t[f][1] = a1 + b1;
@@ -193,15 +241,18 @@ gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
 #pragma unroll
         for (int q = 0; q < 4; ++q) carry[f][q] = T(0);
 
-    // halo layer below the chunk (its top contributions complete plane z0)
+    // prologue: the halo layer below the chunk (its top contributions complete
+    // plane z0), the bottom tuples of plane z0, and plane z0 + 1 in buffer 0
+    int buf = 0;
     if (layer_exists(z0 - 1)) {
-        load_plane(z0 - 1);
+        fetch(z0 - 1);
+        store(1);
         __syncthreads();
-        fwd_xy(tb);
+        fwd_xy(1, tb);
+        fetch(z0);
+        store(0);
         __syncthreads();
-        load_plane(z0);
-        __syncthreads();
-        fwd_xy(tt);
+        fwd_xy(0, tt);
         if (fval) {
             T ob[NO][4];
             element(tb, tt, z0 - 1, ob, carry);
@@ -211,12 +262,21 @@ gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
 #pragma unroll
             for (int q = 0; q < 4; ++q) tb[f][q] = tt[f][q];
     } else {
-        load_plane(z0);
+        fetch(z0);
+        store(0);
         __syncthreads();
-        fwd_xy(tb);
+        fwd_xy(0, tb);
     }
+    __syncthreads();
+    if (z0 + 1 < g.nplanes) fetch(z0 + 1);
+    store(buf);
 
+    double dot = 0.0;
     for (int kk = z0; kk < z1; ++kk) {
+        // buffer `buf` holds plane kk + 1 (if it exists); fetch plane kk + 2
+        const bool need_next = kk + 2 < g.nplanes && kk + 2 <= z1;
+        if (need_next) fetch(kk + 2);
+        __syncthreads();
         T ob[NO][4], ot[NO][4];
 #pragma unroll
         for (int f = 0; f < NO; ++f)
@@ -224,10 +284,7 @@ gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
             for (int q = 0; q < 4; ++q) { ob[f][q] = T(0); ot[f][q] = T(0); }
         const bool up = layer_exists(kk);
         if (up) {
-            __syncthreads();
-            load_plane(kk + 1);
-            __syncthreads();
-            fwd_xy(tt);
+            fwd_xy(buf, tt);
             if (fval) element(tb, tt, kk, ob, ot);
 #pragma unroll
             for (int f = 0; f < NI; ++f)
@@ -235,13 +292,9 @@ gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
                 for (int q = 0; q < 4; ++q) tb[f][q] = tt[f][q];
         } else if (kk + 1 < z1) {
             // fault gap: the next plane starts a new block of elements
-            __syncthreads();
-            load_plane(kk + 1);
-            __syncthreads();
-            fwd_xy(tb);
+            fwd_xy(buf, tb);
         }
         // complete face tuples of plane kk, inverse xy transform to corner values
-        __syncthreads();
 #pragma unroll
         for (int f = 0; f < NO; ++f) {
             const T o0 = carry[f][0] + ob[f][0], o1 = carry[f][1] + ob[f][1];
@@ -254,6 +307,7 @@ gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
 #pragma unroll
             for (int q = 0; q < 4; ++q) carry[f][q] = up ? ot[f][q] : T(0);
         }
+        if (need_next) store(buf ^ 1);
         __syncthreads();
         // node stage: node (tx, ty) of the tile sums its four faces
         if (tx >= 1 && ty >= 1) {
@@ -261,19 +315,49 @@ gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
             if (gi <= g.nx && gj <= g.ny) {
                 const long long node = gi + rowlen * (gj + (long long)(g.ny + 1) * kk);
                 const unsigned m = a.mask[node];
+                const bool lip = g.kf >= 0 && (kk == g.kf || kk == g.kf + 1);
 #pragma unroll
                 for (int f = 0; f < NO; ++f) {
                     const T v = s_face[f][0][tid] + s_face[f][1][tid - 1] +
                                 s_face[f][2][tid - 16] + s_face[f][3][tid - 17];
                     if (OUT_U && f < 3) {
-                        a.yu[f * N + node] = ((m >> f) & 1u) ? T(0) : v;
+                        const T y = ((m >> f) & 1u) ? T(0) : v;
+                        a.yu[f * N + node] = y;
+                        if constexpr (PCG) {
+                            const T pn = ((m >> f) & 1u) ? T(0) : in_u(f, node);
+                            a.pu_new[f * N + node] = pn;
+                            if (!lip) dot += (double)pn * (double)y;
+                        }
                     } else {
                         // raw value on a tied slave lip: the fault kernel folds it
                         const bool slave = g.tied && kk == g.kf + 1;
-                        a.yp[node] = (!slave && ((m >> 3) & 1u)) ? T(0) : v;
+                        const T y = (!slave && ((m >> 3) & 1u)) ? T(0) : v;
+                        a.yp[node] = y;
+                        if constexpr (PCG) {
+                            const T pn = (slave || ((m >> 3) & 1u)) ? T(0) : in_p(node);
+                            a.pp_new[node] = pn;
+                            if (!lip) dot += (double)pn * (double)y;
+                        }
                     }
                 }
             }
+        }
+        buf ^= 1;
+    }
+
+    if constexpr (PCG) {
+        // per-CTA partial of p . Ap (fixed order: warp shuffles, then warps)
+        __shared__ double sh[8];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
+        if ((tid & 31) == 0) sh[tid >> 5] = dot;
+        __syncthreads();
+        if (tid == 0) {
+            double sacc = 0.0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) sacc += sh[w];
+            const int cta = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+            a.part[cta] = sacc;
         }
     }
 }

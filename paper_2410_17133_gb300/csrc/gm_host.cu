@@ -787,6 +787,15 @@ int bind_impl(gm_ctx* c)
     // device allocation
     const long long P = c->P;
     const long long N3 = 3 * N;
+    // reduction partials: the fixed-grid reductions use 2 * GM_RED_BLOCKS slots,
+    // a fused PCG step one per bulk CTA plus one per fault block
+    const int gxp = (c->nx + 1 + 14) / 15, gyp = (c->ny + 1 + 14) / 15;
+    const long long xyp = (long long)gxp * gyp;
+    const long long nzc = std::max(1LL, (4LL * c->sm_count + xyp - 1) / xyp);
+    const long long zcp = std::max(4LL, (c->g.nplanes + nzc - 1) / nzc);
+    c->bulk_grid = (int)(xyp * ((c->g.nplanes + zcp - 1) / zcp));
+    const size_t part_bytes = (size_t)8 * std::max<long long>(4LL * GM_RED_BLOCKS,
+                                                              c->bulk_grid + (c->g.nb + 255) / 256 + 64);
     struct A_ { DevBuf* b; size_t bytes; } allocs[] = {
         {&c->dE64, (size_t)nel * 8}, {&c->dK64, (size_t)nel * 8},
         {&c->dE32, (size_t)nel * 4}, {&c->dK32, (size_t)nel * 4},
@@ -800,17 +809,20 @@ int bind_impl(gm_ctx* c)
         {&c->ddiagK, (size_t)N3 * 8}, {&c->ddiagA, (size_t)N * 8},
         {&c->dKinv64, (size_t)12 * N * 8}, {&c->dKinv32, (size_t)6 * N * 4},
         {&c->dAinv64, (size_t)N * 8}, {&c->dAinv32, (size_t)N * 4},
-        {&c->dscal, (size_t)16 * sizeof(PcgScalars)}, {&c->dpart, (size_t)4 * GM_RED_BLOCKS * 8},
+        {&c->dscal, (size_t)16 * sizeof(PcgScalars)}, {&c->dpart, part_bytes},
         {&c->dcount, (size_t)64},
         {&c->w_du, (size_t)N3 * 8}, {&c->w_dp, (size_t)N * 8}, {&c->w_ut, (size_t)N3 * 8},
         {&c->w_pt, (size_t)N * 8}, {&c->w_b, (size_t)4 * N * 8}, {&c->w_x, (size_t)4 * N * 8},
         {&c->w_y1u, (size_t)N3 * 8}, {&c->w_y1p, (size_t)N * 8}, {&c->w_y2p, (size_t)N * 8},
         {&c->k_r, (size_t)N3 * 8}, {&c->k_z, (size_t)N3 * 8}, {&c->k_p, (size_t)N3 * 8},
+        {&c->k_p2, (size_t)N3 * 8},
         {&c->k_q, (size_t)N3 * 8}, {&c->a_r, (size_t)N * 8}, {&c->a_z, (size_t)N * 8},
-        {&c->a_p, (size_t)N * 8}, {&c->a_q, (size_t)N * 8},
+        {&c->a_p, (size_t)N * 8}, {&c->a_p2, (size_t)N * 8}, {&c->a_q, (size_t)N * 8},
         {&c->k_r32, (size_t)N3 * 4}, {&c->k_z32, (size_t)N3 * 4}, {&c->k_p32, (size_t)N3 * 4},
+        {&c->k_pb32, (size_t)N3 * 4},
         {&c->k_q32, (size_t)N3 * 4}, {&c->k_x32, (size_t)N3 * 4}, {&c->k_b32, (size_t)N3 * 4},
         {&c->a_r32, (size_t)N * 4}, {&c->a_z32, (size_t)N * 4}, {&c->a_p32, (size_t)N * 4},
+        {&c->a_pb32, (size_t)N * 4},
         {&c->a_q32, (size_t)N * 4}, {&c->a_x32, (size_t)N * 4}, {&c->a_b32, (size_t)N * 4},
         {&c->o_y1, (size_t)N3 * 8}, {&c->o_w, (size_t)N3 * 8}, {&c->o_t3, (size_t)N3 * 8},
         {&c->o_r, (size_t)N * 8}, {&c->o_z, (size_t)N * 8}, {&c->o_zold, (size_t)N * 8},

@@ -99,6 +99,11 @@ __host__ __device__ constexpr SecTab gm_make_sectab(int cls) {
 // ---------------------------------------------------------------------------
 // Kernel argument blocks
 // ---------------------------------------------------------------------------
+struct PcgScalars {
+    double rz, pq, alpha, beta, rr, rr0, tol2, pad;
+    int it, done, status, pad2;
+};
+
 struct GridDesc {
     int nx, ny, nz, nplanes;
     int kf;          // lower-lip extended plane, -1 without fault
@@ -120,6 +125,14 @@ struct BulkArgs {
     const uint8_t* mask;
     T cK, cApu, cAup, cS, cC;   // alpha and 1/M folded in by the host
     const int* skip; // if non-null and *skip != 0 the kernel returns at once
+    // PCG mode: input p = z + beta * x (x = p_old), p written to p*_new,
+    // per-CTA partial of p.(A p) over non-lip nodes written to part[cta]
+    const T* zu;
+    const T* zp;
+    T* pu_new;
+    T* pp_new;
+    const double* beta;
+    double* part;
 };
 
 template <typename T>
@@ -139,6 +152,12 @@ struct FaultArgs {
     T tcoef;         // k_perp / (mu_f w0)
     T Lf[16];        // reference quad Laplacian (coefficient 1)
     const int* skip;
+    // PCG mode: add p.(A p) over the lip nodes to the bulk partials and let the
+    // last block form p.Ap and alpha = (r.z)/(p.Ap) in *sc
+    double* part;        // bulk partials at [0, nbulk), this kernel's at [nbulk, ...)
+    int nbulk;
+    unsigned* counter;
+    PcgScalars* sc;
 };
 
 struct LawArgs {
@@ -162,10 +181,6 @@ struct LawArgs {
     float* D32;              // 6P (or null)
 };
 
-struct PcgScalars {
-    double rz, pq, alpha, beta, rr, rr0, tol2, pad;
-    int it, done, status, pad2;
-};
 
 // ---------------------------------------------------------------------------
 // Device buffer
@@ -235,9 +250,10 @@ struct gm_ctx {
     DevBuf dcount;                                     // last-block counters
     // work vectors (FP64)
     DevBuf w_du, w_dp, w_ut, w_pt, w_b, w_x, w_y1u, w_y1p, w_y2u, w_y2p;
-    DevBuf k_r, k_z, k_p, k_q, a_r, a_z, a_p, a_q;     // inner PCG (FP64)
-    DevBuf k_r32, k_z32, k_p32, k_q32, k_x32, k_b32;   // inner PCG (FP32)
-    DevBuf a_r32, a_z32, a_p32, a_q32, a_x32, a_b32;
+    DevBuf k_r, k_z, k_p, k_p2, k_q, a_r, a_z, a_p, a_p2, a_q;     // inner PCG (FP64)
+    DevBuf k_r32, k_z32, k_p32, k_pb32, k_q32, k_x32, k_b32;      // inner PCG (FP32)
+    DevBuf a_r32, a_z32, a_p32, a_pb32, a_q32, a_x32, a_b32;
+    int bulk_grid = 0;                                 // CTAs of one bulk apply
     DevBuf o_y1, o_w, o_x1, o_t3, o_r, o_z, o_zold, o_p, o_q, o_x2, o_t1;   // outer CG
     DevBuf dprevstate;
     void* hpin = nullptr;                              // pinned host scratch (4 KB)
@@ -289,12 +305,14 @@ int gm_launch_count_changes(gm_ctx* c, const int8_t* a, const int8_t* b, int* ou
 // Linear algebra
 int gm_launch_pcg_init(gm_ctx* c, int which, int prec, const void* b, const void* q, void* r,
                        void* z, void* p, double rtol, PcgScalars* sc, cudaStream_t s);
-int gm_launch_pcg_alpha(gm_ctx* c, int which, int prec, const void* p, const void* q,
-                        PcgScalars* sc, cudaStream_t s);
+// One fused PCG operator step: p_new = z + beta p_old, q = A p_new, and
+// alpha = (r.z)/(p_new.q) into *sc (which 0: K_T, which 1: A22).
+int gm_launch_pcg_apply_f64(gm_ctx* c, int which, const double* z, const double* p_old,
+                            double* p_new, double* q, PcgScalars* sc, cudaStream_t s);
+int gm_launch_pcg_apply_f32(gm_ctx* c, int which, const float* z, const float* p_old,
+                            float* p_new, float* q, PcgScalars* sc, cudaStream_t s);
 int gm_launch_pcg_update(gm_ctx* c, int which, int prec, void* x, void* r, void* z,
                          const void* p, const void* q, PcgScalars* sc, int maxit, cudaStream_t s);
-int gm_launch_pcg_dir(gm_ctx* c, int which, int prec, void* p, const void* z, PcgScalars* sc,
-                      cudaStream_t s);
 // y = a*x + b*y over n doubles; z = x + y etc.
 int gm_launch_axpby(gm_ctx* c, long long n, double a, const double* x, double b, double* y,
                     cudaStream_t s);

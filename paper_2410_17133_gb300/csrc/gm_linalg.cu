@@ -1,9 +1,10 @@
 // Preconditioned-CG vector kernels with fused, deterministic FP64 reductions.
 //
 // One PCG iteration (Hestenes-Stiefel, as used inside the partitioned scheme of
-// Sec. 3.3.2) is: q = A p (apply kernels);  alpha = (r.z)/(p.q);
-// x += alpha p, r -= alpha q, z = M^-1 r with the new r.z and r.r in the same
-// pass;  beta = (r.z)_new/(r.z);  p = z + beta p.  The scalars live on the
+// Sec. 3.3.2) takes two fused passes: the operator kernels form the direction
+// p = z + beta p_old, q = A p and alpha = (r.z)/(p.q) (gm_apply.cuh); then
+// x += alpha p, r -= alpha q, z = M^-1 r with the new r.z and r.r in one pass
+// here, whose last block sets beta = (r.z)_new/(r.z).  The scalars live on the
 // device (PcgScalars) so iterations can be enqueued back to back; every kernel
 // returns at once when `done` is set, so the host only checks now and then.
 // Vectors may be FP32 (mixed precision) or FP64; dots always accumulate in FP64.
@@ -111,7 +112,7 @@ gm_pcg_init_kernel(long long N, const T* b, const T* q, T* r, T* z, T* p, const 
         for (int c = 0; c < NC; ++c) {
             r[c * N + n] = rr[c];
             z[c * N + n] = zz[c];
-            p[c * N + n] = zz[c];
+            p[c * N + n] = T(0);   // previous direction: the first step is p = z
             // products of T values are exact in double; the sums accumulate in FP64
             v[0] += (double)rr[c] * (double)zz[c];
             v[1] += (double)rr[c] * (double)rr[c];
@@ -127,29 +128,6 @@ gm_pcg_init_kernel(long long N, const T* b, const T* q, T* r, T* z, T* p, const 
         sc->done = (v[1] == 0.0 || sc->status != GM_OK) ? 1 : 0;
         sc->alpha = 0.0;
         sc->beta = 0.0;
-    }
-}
-
-template <typename T, int WHICH>
-__global__ void __launch_bounds__(256)
-gm_pcg_alpha_kernel(long long N, const T* p, const T* q, PcgScalars* sc, RedCtx rc)
-{
-    constexpr int NC = Prec<T, WHICH>::NC;
-    if (sc->done) return;
-    double v[1] = {0.0};
-    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x)
-#pragma unroll
-        for (int c = 0; c < NC; ++c) v[0] += (double)p[c * N + n] * (double)q[c * N + n];
-    if (gm_grid_sum_l<1>(v, rc.part, rc.counter)) {
-        sc->pq = v[0];
-        if (!(v[0] > 0.0) || !isfinite(v[0])) {
-            sc->status = isfinite(v[0]) ? GM_ENOCONV : GM_ENAN;
-            sc->done = 1;
-            sc->alpha = 0.0;
-        } else {
-            sc->alpha = sc->rz / v[0];
-        }
     }
 }
 
@@ -198,38 +176,10 @@ gm_pcg_update_kernel(long long N, T* x, T* r, T* z, const T* p, const T* q, cons
     }
 }
 
-template <typename T, int WHICH>
-__global__ void __launch_bounds__(256)
-gm_pcg_dir_kernel(long long N, T* p, const T* z, const PcgScalars* sc)
-{
-    constexpr int NC = Prec<T, WHICH>::NC;
-    if (sc->done) return;
-    const T beta = (T)sc->beta;
-    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x)
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const long long k = c * N + n;
-            p[k] = fma(beta, p[k], z[k]);
-        }
-}
-
 static RedCtx redctx(gm_ctx* c)
 {
     return RedCtx{c->dpart.as<double>(), c->dcount.as<unsigned>()};
 }
-
-// which: 0 = K_T (3 comps), 1 = A22; prec: GM_F64 / GM_F32
-#define GM_PCG_DISPATCH(KERNEL, ...)                                                          \
-    do {                                                                                      \
-        if (prec == GM_F64) {                                                                 \
-            if (which == 0) KERNEL<double, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(__VA_ARGS__); \
-            else KERNEL<double, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(__VA_ARGS__);   \
-        } else {                                                                              \
-            if (which == 0) KERNEL<float, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(__VA_ARGS__); \
-            else KERNEL<float, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(__VA_ARGS__);    \
-        }                                                                                     \
-    } while (0)
 
 template <typename T>
 static const T* prec_ptr(gm_ctx* c, int which)
@@ -266,22 +216,6 @@ int gm_launch_pcg_init(gm_ctx* c, int which, int prec, const void* b, const void
     return GM_OK;
 }
 
-int gm_launch_pcg_alpha(gm_ctx* c, int which, int prec, const void* p, const void* q,
-                        PcgScalars* sc, cudaStream_t s)
-{
-    const long long N = c->N;
-    RedCtx rc = redctx(c);
-    if (prec == GM_F64) {
-        if (which == 0) gm_pcg_alpha_kernel<double, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (const double*)p, (const double*)q, sc, rc);
-        else gm_pcg_alpha_kernel<double, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (const double*)p, (const double*)q, sc, rc);
-    } else {
-        if (which == 0) gm_pcg_alpha_kernel<float, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (const float*)p, (const float*)q, sc, rc);
-        else gm_pcg_alpha_kernel<float, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (const float*)p, (const float*)q, sc, rc);
-    }
-    GM_LAUNCHED(c);
-    return GM_OK;
-}
-
 int gm_launch_pcg_update(gm_ctx* c, int which, int prec, void* x, void* r, void* z, const void* p,
                          const void* q, PcgScalars* sc, int maxit, cudaStream_t s)
 {
@@ -305,21 +239,6 @@ int gm_launch_pcg_update(gm_ctx* c, int which, int prec, void* x, void* r, void*
             gm_pcg_update_kernel<float, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
                 N, (float*)x, (float*)r, (float*)z, (const float*)p, (const float*)q,
                 prec_ptr<float>(c, 1), sc, maxit, rc);
-    }
-    GM_LAUNCHED(c);
-    return GM_OK;
-}
-
-int gm_launch_pcg_dir(gm_ctx* c, int which, int prec, void* p, const void* z, PcgScalars* sc,
-                      cudaStream_t s)
-{
-    const long long N = c->N;
-    if (prec == GM_F64) {
-        if (which == 0) gm_pcg_dir_kernel<double, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (double*)p, (const double*)z, sc);
-        else gm_pcg_dir_kernel<double, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (double*)p, (const double*)z, sc);
-    } else {
-        if (which == 0) gm_pcg_dir_kernel<float, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (float*)p, (const float*)z, sc);
-        else gm_pcg_dir_kernel<float, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(N, (float*)p, (const float*)z, sc);
     }
     GM_LAUNCHED(c);
     return GM_OK;

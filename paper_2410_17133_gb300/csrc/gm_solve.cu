@@ -33,12 +33,13 @@ int gm_pcg(gm_ctx* c, int which, int prec, const double* b, double* x, double rt
     const long long n = (which == 0 ? 3 : 1) * c->N;
     PcgScalars* sc = scal(c, which);
     int rc;
-    void *r, *z, *p, *q, *xx;
+    void *r, *z, *p, *p2, *q, *xx;
     const void* bb;
     if (prec == GM_F64) {
         r = (which == 0 ? c->k_r : c->a_r).p;
         z = (which == 0 ? c->k_z : c->a_z).p;
         p = (which == 0 ? c->k_p : c->a_p).p;
+        p2 = (which == 0 ? c->k_p2 : c->a_p2).p;
         q = (which == 0 ? c->k_q : c->a_q).p;
         xx = x;
         bb = b;
@@ -49,6 +50,7 @@ int gm_pcg(gm_ctx* c, int which, int prec, const double* b, double* x, double rt
         r = (which == 0 ? c->k_r32 : c->a_r32).p;
         z = (which == 0 ? c->k_z32 : c->a_z32).p;
         p = (which == 0 ? c->k_p32 : c->a_p32).p;
+        p2 = (which == 0 ? c->k_pb32 : c->a_pb32).p;
         q = (which == 0 ? c->k_q32 : c->a_q32).p;
         xx = (which == 0 ? c->k_x32 : c->a_x32).p;
         float* b32 = (which == 0 ? c->k_b32 : c->a_b32).as<float>();
@@ -65,12 +67,21 @@ int gm_pcg(gm_ctx* c, int which, int prec, const double* b, double* x, double rt
     }
     PcgScalars* hs = static_cast<PcgScalars*>(c->hpin);
     int batch = 4;
+    void* pp[2] = {p, p2};   // search direction, double-buffered across iterations
+    int cur = 0;
     for (;;) {
         for (int k = 0; k < batch; ++k) {
-            if ((rc = apply_inner(c, which, prec, p, q, s, &sc->done))) return rc;
-            if ((rc = gm_launch_pcg_alpha(c, which, prec, p, q, sc, s))) return rc;
-            if ((rc = gm_launch_pcg_update(c, which, prec, xx, r, z, p, q, sc, maxit, s))) return rc;
-            if ((rc = gm_launch_pcg_dir(c, which, prec, p, z, sc, s))) return rc;
+            void* pold = pp[cur];
+            void* pnew = pp[cur ^ 1];
+            if (prec == GM_F64)
+                rc = gm_launch_pcg_apply_f64(c, which, (const double*)z, (const double*)pold,
+                                             (double*)pnew, (double*)q, sc, s);
+            else
+                rc = gm_launch_pcg_apply_f32(c, which, (const float*)z, (const float*)pold,
+                                             (float*)pnew, (float*)q, sc, s);
+            if (rc) return rc;
+            if ((rc = gm_launch_pcg_update(c, which, prec, xx, r, z, pnew, q, sc, maxit, s))) return rc;
+            cur ^= 1;
         }
         GM_CUDA_TRY(c, cudaMemcpyAsync(hs, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
         GM_CUDA_TRY(c, cudaStreamSynchronize(s));
