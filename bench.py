@@ -184,6 +184,22 @@ def log(*a):
     print("[bench]", *a, file=sys.stderr, flush=True)
 
 
+def max_over_ranks(ms, dist, device):
+    """Largest per-rank timed-region duration (all ranks get it)."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(ndof_per_rank, steps, world, max_ms):
+    """GDoF/s of the whole job: every rank solves its own replica of the
+    workload (weak scaling), so the work is world x ndof x steps."""
+    return ndof_per_rank * steps * world / (max_ms * 1e-3) / 1e9
+
+
 def run_gm(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -243,12 +259,8 @@ def run_gm(args, rank, world, local_rank):
     l1, _ = s.counters()
     launches = l1 - l0
     log("timed steps", ms)
-    total_ms = sum(ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ndof * K * world / (total_ms * 1e-3) / 1e9
+    total_ms = max_over_ranks(sum(ms), dist, "cuda")
+    value = whole_job_value(ndof, K, world, total_ms)
 
     # plain FP64 solver on the same steps (fresh state advanced by the same warm-up)
     fp64 = None
