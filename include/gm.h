@@ -94,6 +94,9 @@ typedef struct {
     int inner_maxit;
     int precision;           /* GM_F64, or GM_F32: FP32 operators + preconditioners
                                 inside the FP64 Newton/refinement loop */
+    int schur_precond;       /* 0: A22^-1 (Sec. 3.3.2); 1: (A22 + sum_e alpha^2/K_dr,e M_e)^-1,
+                                the fixed-stress approximation of the Schur complement
+                                (same solution, fewer outer iterations under strong coupling) */
 } gm_step_opts;
 
 typedef struct {

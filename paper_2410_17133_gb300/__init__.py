@@ -44,7 +44,7 @@ class StepOpts(C.Structure):
     _fields_ = [("newton_rtol", C.c_double), ("newton_maxit", C.c_int),
                 ("outer_rtol", C.c_double), ("outer_maxit", C.c_int),
                 ("inner_rtol", C.c_double), ("inner_maxit", C.c_int),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("schur_precond", C.c_int)]
 
 
 class StepReport(C.Structure):
@@ -277,15 +277,19 @@ class Solver:
         return b, rh.value
 
     def step(self, dt, newton_rtol=None, precision=F64, newton_maxit=50, outer_rtol=None,
-             outer_maxit=500, inner_rtol=None, inner_maxit=20000, stream=None):
-        if newton_rtol is None and outer_rtol is None and inner_rtol is None and precision == F64:
+             outer_maxit=500, inner_rtol=None, inner_maxit=20000, schur_precond=0, stream=None):
+        """One implicit step.  schur_precond 0: A22^-1 preconditioner of the
+        partitioned CG (the paper's); 1: fixed-stress augmented A22."""
+        if (newton_rtol is None and outer_rtol is None and inner_rtol is None and precision == F64
+                and schur_precond == 0):
             opts = None
         else:
             d_outer = 1e-8 if precision == F64 else 1e-4
             d_inner = 1e-10 if precision == F64 else 1e-5
             opts = StepOpts(1e-10 if newton_rtol is None else newton_rtol, newton_maxit,
                             d_outer if outer_rtol is None else outer_rtol, outer_maxit,
-                            d_inner if inner_rtol is None else inner_rtol, inner_maxit, precision)
+                            d_inner if inner_rtol is None else inner_rtol, inner_maxit, precision,
+                            schur_precond)
         rep = StepReport()
         self._chk(self._L.gm_partitioned_step(self.h, float(dt), None if opts is None else C.byref(opts),
                                               C.byref(rep), _stream_ptr(stream)))

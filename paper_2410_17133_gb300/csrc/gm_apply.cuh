@@ -262,6 +262,7 @@ inline BulkArgs<T> gm_bulk_args(gm_ctx* c, double cK, double cApu, double cAup, 
     b.skip = nullptr;
     b.zu = nullptr; b.zp = nullptr; b.pu_new = nullptr; b.pp_new = nullptr;
     b.beta = nullptr; b.part = nullptr;
+    b.fs = nullptr; b.cFS = T(0);
     return b;
 }
 
@@ -313,7 +314,8 @@ static void gm_apply_dispatch_cls(gm_ctx* c, const RefOps<T>& R, double cK, doub
 // Fused PCG operator step for K_T (which 0) or A22 (which 1).
 template <typename T, int CLS, int MODE>
 static void gm_pcg_apply_t(gm_ctx* c, const RefOps<T>& R, const T* z, const T* p_old, T* p_new, T* q,
-                           const T* E, const T* kap, const T* D, PcgScalars* sc, cudaStream_t s)
+                           const T* E, const T* kap, const T* D, PcgScalars* sc, cudaStream_t s,
+                           const T* fs)
 {
     constexpr bool U = (MODE & GM_M_K) != 0;
     const double cK = U ? 1.0 : 0.0, cS = U ? 0.0 : 1.0, cC = U ? 0.0 : c->dt;
@@ -326,6 +328,8 @@ static void gm_pcg_apply_t(gm_ctx* c, const RefOps<T>& R, const T* z, const T* p
     b.skip = &sc->done;
     b.beta = &sc->beta;
     b.part = part;
+    b.fs = fs;
+    b.cFS = T(1);
     if (U) { b.xu = p_old; b.zu = z; b.pu_new = p_new; b.yu = q; b.xp = nullptr; b.yp = nullptr; }
     else { b.xp = p_old; b.zp = z; b.pp_new = p_new; b.yp = q; b.xu = nullptr; b.yu = nullptr; }
     constexpr int BULK = MODE & (GM_M_K | GM_M_S | GM_M_C);
@@ -354,11 +358,11 @@ static void gm_pcg_apply_t(gm_ctx* c, const RefOps<T>& R, const T* z, const T* p
 template <typename T, int MODE>
 static void gm_pcg_apply_dispatch(gm_ctx* c, const RefOps<T>& R, const T* z, const T* p_old, T* p_new,
                                   T* q, const T* E, const T* kap, const T* D, PcgScalars* sc,
-                                  cudaStream_t s)
+                                  cudaStream_t s, const T* fs)
 {
     switch (c->cls) {
-    case GM_CLS_BOX: gm_pcg_apply_t<T, GM_CLS_BOX, MODE>(c, R, z, p_old, p_new, q, E, kap, D, sc, s); break;
-    case GM_CLS_MONO: gm_pcg_apply_t<T, GM_CLS_MONO, MODE>(c, R, z, p_old, p_new, q, E, kap, D, sc, s); break;
-    default: gm_pcg_apply_t<T, GM_CLS_GEN, MODE>(c, R, z, p_old, p_new, q, E, kap, D, sc, s); break;
+    case GM_CLS_BOX: gm_pcg_apply_t<T, GM_CLS_BOX, MODE>(c, R, z, p_old, p_new, q, E, kap, D, sc, s, fs); break;
+    case GM_CLS_MONO: gm_pcg_apply_t<T, GM_CLS_MONO, MODE>(c, R, z, p_old, p_new, q, E, kap, D, sc, s, fs); break;
+    default: gm_pcg_apply_t<T, GM_CLS_GEN, MODE>(c, R, z, p_old, p_new, q, E, kap, D, sc, s, fs); break;
     }
 }

@@ -34,10 +34,12 @@ int gm_launch_pcg_apply_f32(gm_ctx* c, int which, const float* z, const float* p
     const float* E = c->dE32.as<float>();
     const float* kap = c->dK32.as<float>();
     const float* D = c->dD32.as<float>();
+    // which 0: K_T; 1: A22; 2: A22 plus the fixed-stress storage term
     if (which == 0)
-        gm_pcg_apply_dispatch<float, GM_MODE_KT>(c, c->R32, z, p_old, p_new, q, E, kap, D, sc, s);
+        gm_pcg_apply_dispatch<float, GM_MODE_KT>(c, c->R32, z, p_old, p_new, q, E, kap, D, sc, s, nullptr);
     else
-        gm_pcg_apply_dispatch<float, GM_MODE_A22>(c, c->R32, z, p_old, p_new, q, E, kap, D, sc, s);
+        gm_pcg_apply_dispatch<float, GM_MODE_A22>(c, c->R32, z, p_old, p_new, q, E, kap, D, sc, s,
+                                                  which == 2 ? c->dFS32.as<float>() : nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return c->set_err(GM_ECUDA, std::string("pcg apply launch: ") + cudaGetErrorString(e));
     return GM_OK;

@@ -35,10 +35,12 @@ int gm_launch_pcg_apply_f64(gm_ctx* c, int which, const double* z, const double*
     const double* E = c->dE64.as<double>();
     const double* kap = c->dK64.as<double>();
     const double* D = c->dD64.as<double>();
+    // which 0: K_T; 1: A22; 2: A22 plus the fixed-stress storage term
     if (which == 0)
-        gm_pcg_apply_dispatch<double, GM_MODE_KT>(c, c->R64, z, p_old, p_new, q, E, kap, D, sc, s);
+        gm_pcg_apply_dispatch<double, GM_MODE_KT>(c, c->R64, z, p_old, p_new, q, E, kap, D, sc, s, nullptr);
     else
-        gm_pcg_apply_dispatch<double, GM_MODE_A22>(c, c->R64, z, p_old, p_new, q, E, kap, D, sc, s);
+        gm_pcg_apply_dispatch<double, GM_MODE_A22>(c, c->R64, z, p_old, p_new, q, E, kap, D, sc, s,
+                                                  which == 2 ? c->dFS64.as<double>() : nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return c->set_err(GM_ECUDA, std::string("pcg apply launch: ") + cudaGetErrorString(e));
     return GM_OK;

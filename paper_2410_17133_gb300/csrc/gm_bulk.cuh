@@ -162,9 +162,10 @@ gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
 #pragma unroll
             for (int q = 0; q < 4; ++q) { ob[f][q] = T(0); ot[f][q] = T(0); }
         const long long e = fi + (long long)g.nx * (fj + (long long)g.ny * layer_index(kb));
-        T kE = T(0), kC = T(0);
+        T kE = T(0), kC = T(0), kS = T(0);
         if constexpr (DO_K) kE = a.cK * a.E[e];
         if constexpr (DO_C) kC = a.cC * a.kap[e];
+        if constexpr (DO_S) kS = a.fs != nullptr ? a.cS + a.cFS * a.fs[e] : a.cS;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             T xu[BU > 0 ? BU : 1];
@@ -218,7 +219,7 @@ gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
                         T t = T(0);
 #pragma unroll
                         for (int j2 = 0; j2 < BP; ++j2) t = fma(R.M[(b * BP + j) * BP + j2], xp[j2], t);
-                        acc = fma(a.cS, t, acc);
+                        acc = fma(kS, t, acc);
                     }
                     if constexpr (DO_C) {
                         T t = T(0);

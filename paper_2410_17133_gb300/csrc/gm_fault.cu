@@ -304,6 +304,9 @@ struct DiagArgs {
     double* dA;       // N
     double* Ainv64;   // N
     float* Ainv32;    // N
+    const double* fs;     // per-element fixed-stress storage coefficient
+    double* Afsinv64;     // N, Jacobi of A22 + fixed-stress term
+    float* Afsinv32;
 };
 
 __global__ void __launch_bounds__(256) gm_diag_kernel(const DiagArgs a)
@@ -315,7 +318,7 @@ __global__ void __launch_bounds__(256) gm_diag_kernel(const DiagArgs a)
     const long long pid = n - kk * a.g.nb;
     const int i = (int)(pid % (a.g.nx + 1)), j = (int)(pid / (a.g.nx + 1));
     double K9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    double dA = 0.0;
+    double dA = 0.0, dfs = 0.0;
     const bool slave = a.g.tied && kk == a.g.kf + 1;
     auto add_layer = [&](int kb, int az, bool mech) {
         if (kb < 0 || kb + 1 >= a.g.nplanes || kb == a.g.kf) return;
@@ -331,6 +334,7 @@ __global__ void __launch_bounds__(256) gm_diag_kernel(const DiagArgs a)
                     for (int q = 0; q < 9; ++q) K9[q] += E * a.Kblk[loc][q];
                 }
                 dA += a.invM * a.Md[loc] + a.dt * a.kap[e] * a.Ld[loc];
+                dfs += a.fs[e] * a.Md[loc];
             }
     };
     add_layer((int)kk - 1, 1, true);
@@ -362,6 +366,8 @@ __global__ void __launch_bounds__(256) gm_diag_kernel(const DiagArgs a)
     a.dA[n] = pfree ? dA : 1.0;
     a.Ainv64[n] = pfree ? 1.0 / dA : 0.0;
     a.Ainv32[n] = pfree ? (float)(1.0 / dA) : 0.0f;
+    a.Afsinv64[n] = pfree ? 1.0 / (dA + dfs) : 0.0;
+    a.Afsinv32[n] = pfree ? (float)(1.0 / (dA + dfs)) : 0.0f;
 }
 
 int gm_launch_diag(gm_ctx* c, cudaStream_t s)
@@ -388,6 +394,9 @@ int gm_launch_diag(gm_ctx* c, cudaStream_t s)
     a.dA = c->ddiagA.as<double>();
     a.Ainv64 = c->dAinv64.as<double>();
     a.Ainv32 = c->dAinv32.as<float>();
+    a.fs = c->dFS64.as<double>();
+    a.Afsinv64 = c->dAfsinv64.as<double>();
+    a.Afsinv32 = c->dAfsinv32.as<float>();
     const int nblk = (int)((c->N + 255) / 256);
     gm_diag_kernel<<<nblk, 256, 0, s>>>(a);
     GM_LAUNCHED(c);

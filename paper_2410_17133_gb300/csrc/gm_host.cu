@@ -240,6 +240,8 @@ int gm_destroy(gm_ctx* c)
 {
     if (!c) return GM_OK;
     cudaSetDevice(c->device);
+    c->drop_graphs();
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->hpin) cudaFreeHost(c->hpin);
     delete c;
     return GM_OK;
@@ -541,6 +543,7 @@ extern "C" int gm_partitioned_step(gm_ctx* c, double dt, const gm_step_opts* opt
     o.outer_rtol = 1e-8; o.outer_maxit = 500;
     o.inner_rtol = 1e-10; o.inner_maxit = 20000;
     o.precision = GM_F64;
+    o.schur_precond = 0;
     if (opts) o = *opts;
     if (o.precision == GM_F32 && !opts) { o.inner_rtol = 1e-5; o.outer_rtol = 1e-4; }
     int rc;
@@ -591,7 +594,7 @@ extern "C" int gm_partitioned_step(gm_ctx* c, double dt, const gm_step_opts* opt
         int oit = 0;
         double orr = 0;
         rc = gm_prevost(c, o.precision, b, b + N3, x, x + N3, o.outer_rtol, o.outer_maxit, o.inner_rtol,
-                        o.inner_maxit, &oit, &R.inner_k, &R.inner_a, &orr, s);
+                        o.inner_maxit, &oit, &R.inner_k, &R.inner_a, &orr, s, o.schur_precond);
         if (rc == GM_ENAN) return rc;
         R.outer += oit;
         if ((rc = gm_launch_axpby(c, N3, 1.0, x, 1.0, du, s))) return rc;
@@ -708,6 +711,7 @@ namespace {
 int bind_impl(gm_ctx* c)
 {
     (void)cudaGetLastError();   // start from a clean runtime error state
+    c->drop_graphs();           // graphs hold pointers into the buffers freed below
     if (!c->has_mesh || !c->has_mat) return c->set_err(GM_ESTATE, "bind: mesh and materials required");
     const long long N = n_nodes_of(c);
     const long long nel = (long long)c->nx * c->ny * c->nz;
@@ -809,13 +813,15 @@ int bind_impl(gm_ctx* c)
         {&c->ddiagK, (size_t)N3 * 8}, {&c->ddiagA, (size_t)N * 8},
         {&c->dKinv64, (size_t)12 * N * 8}, {&c->dKinv32, (size_t)6 * N * 4},
         {&c->dAinv64, (size_t)N * 8}, {&c->dAinv32, (size_t)N * 4},
+        {&c->dFS64, (size_t)nel * 8}, {&c->dFS32, (size_t)nel * 4},
+        {&c->dAfsinv64, (size_t)N * 8}, {&c->dAfsinv32, (size_t)N * 4},
         {&c->dscal, (size_t)16 * sizeof(PcgScalars)}, {&c->dpart, part_bytes},
         {&c->dcount, (size_t)64},
         {&c->w_du, (size_t)N3 * 8}, {&c->w_dp, (size_t)N * 8}, {&c->w_ut, (size_t)N3 * 8},
         {&c->w_pt, (size_t)N * 8}, {&c->w_b, (size_t)4 * N * 8}, {&c->w_x, (size_t)4 * N * 8},
         {&c->w_y1u, (size_t)N3 * 8}, {&c->w_y1p, (size_t)N * 8}, {&c->w_y2p, (size_t)N * 8},
         {&c->k_r, (size_t)N3 * 8}, {&c->k_z, (size_t)N3 * 8}, {&c->k_p, (size_t)N3 * 8},
-        {&c->k_p2, (size_t)N3 * 8},
+        {&c->k_p2, (size_t)N3 * 8}, {&c->k_x64, (size_t)N3 * 8}, {&c->a_x64, (size_t)N * 8},
         {&c->k_q, (size_t)N3 * 8}, {&c->a_r, (size_t)N * 8}, {&c->a_z, (size_t)N * 8},
         {&c->a_p, (size_t)N * 8}, {&c->a_p2, (size_t)N * 8}, {&c->a_q, (size_t)N * 8},
         {&c->k_r32, (size_t)N3 * 4}, {&c->k_z32, (size_t)N3 * 4}, {&c->k_p32, (size_t)N3 * 4},
@@ -842,6 +848,15 @@ int bind_impl(gm_ctx* c)
     GM_CUDA_TRY(c, cudaMemcpy(c->dE32.p, f32.data(), nel * 4, cudaMemcpyHostToDevice));
     for (long long e = 0; e < nel; ++e) f32[e] = (float)kap[e];
     GM_CUDA_TRY(c, cudaMemcpy(c->dK32.p, f32.data(), nel * 4, cudaMemcpyHostToDevice));
+    // fixed-stress storage coefficient alpha^2 / K_dr with the drained bulk
+    // modulus K_dr = E / (3 (1 - 2 nu)) of each element
+    {
+        std::vector<double> fs(nel);
+        for (long long e = 0; e < nel; ++e) fs[e] = c->alpha * c->alpha * 3.0 * (1.0 - 2.0 * c->nu) / c->E[e];
+        GM_CUDA_TRY(c, cudaMemcpy(c->dFS64.p, fs.data(), nel * 8, cudaMemcpyHostToDevice));
+        for (long long e = 0; e < nel; ++e) f32[e] = (float)fs[e];
+        GM_CUDA_TRY(c, cudaMemcpy(c->dFS32.p, f32.data(), nel * 4, cudaMemcpyHostToDevice));
+    }
     std::vector<uint8_t> mask(N, 0);
     for (long long n = 0; n < N; ++n)
         for (int f = 0; f < 4; ++f)

@@ -133,6 +133,10 @@ struct BulkArgs {
     T* pp_new;
     const double* beta;
     double* part;
+    // optional per-element extra storage coefficient (fixed-stress term): the
+    // storage block uses cS + cFS * fs[e] instead of cS when fs is non-null
+    const T* fs;
+    T cFS;
 };
 
 template <typename T>
@@ -245,18 +249,33 @@ struct gm_ctx {
     DevBuf du_n, dp_n, ddlie_n, dflags_n;              // accepted state
     DevBuf dstate, dtn, dts, ddlie, dT, dF, ddn, dgs, dD64, dD32;   // fault work
     DevBuf ddiagK, ddiagA, dKinv64, dKinv32, dAinv64, dAinv32;
+    DevBuf dFS64, dFS32, dAfsinv64, dAfsinv32;         // fixed-stress storage term
     DevBuf dscal;                                      // PcgScalars[4] + misc
     DevBuf dpart;                                      // reduction partials
     DevBuf dcount;                                     // last-block counters
     // work vectors (FP64)
     DevBuf w_du, w_dp, w_ut, w_pt, w_b, w_x, w_y1u, w_y1p, w_y2u, w_y2p;
     DevBuf k_r, k_z, k_p, k_p2, k_q, a_r, a_z, a_p, a_p2, a_q;     // inner PCG (FP64)
+    DevBuf k_x64, a_x64;                               // FP64 PCG corrections
     DevBuf k_r32, k_z32, k_p32, k_pb32, k_q32, k_x32, k_b32;      // inner PCG (FP32)
     DevBuf a_r32, a_z32, a_p32, a_pb32, a_q32, a_x32, a_b32;
     int bulk_grid = 0;                                 // CTAs of one bulk apply
     DevBuf o_y1, o_w, o_x1, o_t3, o_r, o_z, o_zold, o_p, o_q, o_x2, o_t1;   // outer CG
     DevBuf dprevstate;
     void* hpin = nullptr;                              // pinned host scratch (4 KB)
+    // CUDA graphs of two fused PCG iterations, per (operator, precision);
+    // captured on a private stream, replayed on the caller's stream
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t pcg_graph[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    double pcg_graph_dt[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    int pcg_graph_maxit[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    long long pcg_graph_launches[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    bool use_graphs = true;
+    void drop_graphs() {
+        for (auto& row : pcg_graph)
+            for (auto& gph : row)
+                if (gph) { cudaGraphExecDestroy(gph); gph = nullptr; }
+    }
     long long applies = 0;                             // bulk apply launches
     long long launches = 0;                            // all kernel launches
 
@@ -325,12 +344,15 @@ int gm_launch_dot(gm_ctx* c, long long n, const double* x, const double* y, cons
 int gm_launch_jacobi_apply(gm_ctx* c, int which, const double* r, double* z, cudaStream_t s);
 
 // Solvers (gm_solve.cu)
+// x_zero: the initial guess is zero (x is overwritten), which skips the
+// initial operator application.  An inner solve that reaches maxit returns
+// GM_ENOCONV with its current iterate in x.
 int gm_pcg(gm_ctx* c, int which, int prec, const double* b, double* x, double rtol, int maxit,
-           int* iters, double* relres, cudaStream_t s);
+           int* iters, double* relres, cudaStream_t s, bool x_zero = false);
 int gm_prevost(gm_ctx* c, int prec, const double* b1, const double* b2, double* x1, double* x2,
                double outer_rtol, int outer_maxit, double inner_rtol, int inner_maxit,
                int* outer_it, long long* inner_k, long long* inner_a, double* relres,
-               cudaStream_t s);
+               cudaStream_t s, int schur_precond = 0);
 
 constexpr int GM_RED_BLOCKS = 608;   // fixed grid of the deterministic reductions
 constexpr int GM_RED_THREADS = 256;

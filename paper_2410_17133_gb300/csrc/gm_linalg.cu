@@ -181,11 +181,14 @@ static RedCtx redctx(gm_ctx* c)
     return RedCtx{c->dpart.as<double>(), c->dcount.as<unsigned>()};
 }
 
+// which 0: K_T block-Jacobi; 1: A22 Jacobi; 2: Jacobi of A22 plus the fixed-stress term
 template <typename T>
 static const T* prec_ptr(gm_ctx* c, int which)
 {
-    if constexpr (sizeof(T) == 8) return which == 0 ? c->dKinv64.as<T>() : c->dAinv64.as<T>();
-    else return which == 0 ? c->dKinv32.as<T>() : c->dAinv32.as<T>();
+    if constexpr (sizeof(T) == 8)
+        return which == 0 ? c->dKinv64.as<T>() : (which == 1 ? c->dAinv64.as<T>() : c->dAfsinv64.as<T>());
+    else
+        return which == 0 ? c->dKinv32.as<T>() : (which == 1 ? c->dAinv32.as<T>() : c->dAfsinv32.as<T>());
 }
 
 int gm_launch_pcg_init(gm_ctx* c, int which, int prec, const void* b, const void* q, void* r,
@@ -201,7 +204,7 @@ int gm_launch_pcg_init(gm_ctx* c, int which, int prec, const void* b, const void
         else
             gm_pcg_init_kernel<double, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
                 N, (const double*)b, (const double*)q, (double*)r, (double*)z, (double*)p,
-                prec_ptr<double>(c, 1), rtol, sc, rc);
+                prec_ptr<double>(c, which), rtol, sc, rc);
     } else {
         if (which == 0)
             gm_pcg_init_kernel<float, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
@@ -210,7 +213,7 @@ int gm_launch_pcg_init(gm_ctx* c, int which, int prec, const void* b, const void
         else
             gm_pcg_init_kernel<float, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
                 N, (const float*)b, (const float*)q, (float*)r, (float*)z, (float*)p,
-                prec_ptr<float>(c, 1), rtol, sc, rc);
+                prec_ptr<float>(c, which), rtol, sc, rc);
     }
     GM_LAUNCHED(c);
     return GM_OK;
@@ -229,7 +232,7 @@ int gm_launch_pcg_update(gm_ctx* c, int which, int prec, void* x, void* r, void*
         else
             gm_pcg_update_kernel<double, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
                 N, (double*)x, (double*)r, (double*)z, (const double*)p, (const double*)q,
-                prec_ptr<double>(c, 1), sc, maxit, rc);
+                prec_ptr<double>(c, which), sc, maxit, rc);
     } else {
         if (which == 0)
             gm_pcg_update_kernel<float, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
@@ -238,7 +241,7 @@ int gm_launch_pcg_update(gm_ctx* c, int which, int prec, void* x, void* r, void*
         else
             gm_pcg_update_kernel<float, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
                 N, (float*)x, (float*)r, (float*)z, (const float*)p, (const float*)q,
-                prec_ptr<float>(c, 1), sc, maxit, rc);
+                prec_ptr<float>(c, which), sc, maxit, rc);
     }
     GM_LAUNCHED(c);
     return GM_OK;

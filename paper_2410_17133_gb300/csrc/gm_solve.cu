@@ -28,24 +28,35 @@ static int apply_inner(gm_ctx* c, int which, int prec, const void* x, void* y, c
 // iteration runs on FP32 vectors and FP32 operators for the correction
 // d = A^-1 (b - A x), added to x in FP64.
 int gm_pcg(gm_ctx* c, int which, int prec, const double* b, double* x, double rtol, int maxit,
-           int* iters, double* relres, cudaStream_t s)
+           int* iters, double* relres, cudaStream_t s, bool x_zero)
 {
     const long long n = (which == 0 ? 3 : 1) * c->N;
     PcgScalars* sc = scal(c, which);
+    // which 2 (A22 plus the fixed-stress term) is only used as a preconditioner
+    // solve from a zero initial guess
+    if (which == 2 && !x_zero) return c->set_err(GM_EINVAL, "PCG: fixed-stress operator needs x0 = 0");
     int rc;
     void *r, *z, *p, *p2, *q, *xx;
     const void* bb;
+    // Both precisions iterate on a correction d from d = 0 in an internal buffer
+    // (so the captured graphs see fixed pointers); x += d at the end.
     if (prec == GM_F64) {
         r = (which == 0 ? c->k_r : c->a_r).p;
         z = (which == 0 ? c->k_z : c->a_z).p;
         p = (which == 0 ? c->k_p : c->a_p).p;
         p2 = (which == 0 ? c->k_p2 : c->a_p2).p;
         q = (which == 0 ? c->k_q : c->a_q).p;
-        xx = x;
+        xx = (which == 0 ? c->k_x64 : c->a_x64).p;
+        GM_CUDA_TRY(c, cudaMemsetAsync(xx, 0, n * sizeof(double), s));
         bb = b;
-        // q = A x for the initial residual
-        if ((rc = apply_inner(c, which, GM_F64, x, q, s, nullptr))) return rc;
-        if ((rc = gm_launch_pcg_init(c, which, GM_F64, bb, q, r, z, p, rtol, sc, s))) return rc;
+        if (x_zero) {
+            GM_CUDA_TRY(c, cudaMemsetAsync(x, 0, n * sizeof(double), s));
+            if ((rc = gm_launch_pcg_init(c, which, GM_F64, bb, nullptr, r, z, p, rtol, sc, s))) return rc;
+        } else {
+            // q = A x for the initial residual
+            if ((rc = apply_inner(c, which, GM_F64, x, q, s, nullptr))) return rc;
+            if ((rc = gm_launch_pcg_init(c, which, GM_F64, bb, q, r, z, p, rtol, sc, s))) return rc;
+        }
     } else {
         r = (which == 0 ? c->k_r32 : c->a_r32).p;
         z = (which == 0 ? c->k_z32 : c->a_z32).p;
@@ -55,12 +66,17 @@ int gm_pcg(gm_ctx* c, int which, int prec, const double* b, double* x, double rt
         xx = (which == 0 ? c->k_x32 : c->a_x32).p;
         float* b32 = (which == 0 ? c->k_b32 : c->a_b32).as<float>();
         // FP64 residual of the initial guess, then FP32 correction solve from 0
-        double* q64 = (which == 0 ? c->k_q : c->a_q).as<double>();
-        if ((rc = apply_inner(c, which, GM_F64, x, q64, s, nullptr))) return rc;
-        double* r64 = (which == 0 ? c->k_r : c->a_r).as<double>();
-        GM_CUDA_TRY(c, cudaMemcpyAsync(r64, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        if ((rc = gm_launch_axpby(c, n, -1.0, q64, 1.0, r64, s))) return rc;
-        if ((rc = gm_launch_copy_cast_d2f(c, n, r64, b32, s))) return rc;
+        if (x_zero) {
+            GM_CUDA_TRY(c, cudaMemsetAsync(x, 0, n * sizeof(double), s));
+            if ((rc = gm_launch_copy_cast_d2f(c, n, b, b32, s))) return rc;
+        } else {
+            double* q64 = (which == 0 ? c->k_q : c->a_q).as<double>();
+            if ((rc = apply_inner(c, which, GM_F64, x, q64, s, nullptr))) return rc;
+            double* r64 = (which == 0 ? c->k_r : c->a_r).as<double>();
+            GM_CUDA_TRY(c, cudaMemcpyAsync(r64, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            if ((rc = gm_launch_axpby(c, n, -1.0, q64, 1.0, r64, s))) return rc;
+            if ((rc = gm_launch_copy_cast_d2f(c, n, r64, b32, s))) return rc;
+        }
         GM_CUDA_TRY(c, cudaMemsetAsync(xx, 0, n * sizeof(float), s));
         bb = b32;
         if ((rc = gm_launch_pcg_init(c, which, GM_F32, bb, nullptr, r, z, p, rtol, sc, s))) return rc;
@@ -68,20 +84,64 @@ int gm_pcg(gm_ctx* c, int which, int prec, const double* b, double* x, double rt
     PcgScalars* hs = static_cast<PcgScalars*>(c->hpin);
     int batch = 4;
     void* pp[2] = {p, p2};   // search direction, double-buffered across iterations
-    int cur = 0;
-    for (;;) {
-        for (int k = 0; k < batch; ++k) {
-            void* pold = pp[cur];
-            void* pnew = pp[cur ^ 1];
+    // two iterations (one per direction buffer): enqueue directly or as a graph
+    auto two_iterations = [&](cudaStream_t st) -> int {
+        int e;
+        for (int k = 0; k < 2; ++k) {
+            void* pold = pp[k];
+            void* pnew = pp[k ^ 1];
             if (prec == GM_F64)
-                rc = gm_launch_pcg_apply_f64(c, which, (const double*)z, (const double*)pold,
-                                             (double*)pnew, (double*)q, sc, s);
+                e = gm_launch_pcg_apply_f64(c, which, (const double*)z, (const double*)pold,
+                                            (double*)pnew, (double*)q, sc, st);
             else
-                rc = gm_launch_pcg_apply_f32(c, which, (const float*)z, (const float*)pold,
-                                             (float*)pnew, (float*)q, sc, s);
-            if (rc) return rc;
-            if ((rc = gm_launch_pcg_update(c, which, prec, xx, r, z, pnew, q, sc, maxit, s))) return rc;
-            cur ^= 1;
+                e = gm_launch_pcg_apply_f32(c, which, (const float*)z, (const float*)pold,
+                                            (float*)pnew, (float*)q, sc, st);
+            if (e) return e;
+            if ((e = gm_launch_pcg_update(c, which, prec, xx, r, z, pnew, q, sc, maxit, st))) return e;
+        }
+        return GM_OK;
+    };
+    cudaGraphExec_t gexec = nullptr;
+    const int pi = prec == GM_F64 ? 0 : 1;
+    if (c->use_graphs) {
+        // the graph bakes in the kernel parameters: dt (A22 operators), maxit and
+        // the solution pointer; rebuild when any of them changes
+        cudaGraphExec_t& slot = c->pcg_graph[which][pi];
+        const double gdt = which == 0 ? 0.0 : c->dt;
+        if (slot && (c->pcg_graph_dt[which][pi] != gdt || c->pcg_graph_maxit[which][pi] != maxit)) {
+            cudaGraphExecDestroy(slot);
+            slot = nullptr;
+        }
+        if (!slot) {
+            if (!c->cap_stream)
+                GM_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+            const long long l0 = c->launches, a0 = c->applies;
+            GM_CUDA_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+            rc = two_iterations(c->cap_stream);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(c->cap_stream, &graph);
+            if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+            if (ec != cudaSuccess) return c->set_err(GM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+            const cudaError_t ei = cudaGraphInstantiate(&slot, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ei != cudaSuccess) { slot = nullptr; return c->set_err(GM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei)); }
+            c->pcg_graph_dt[which][pi] = gdt;
+            c->pcg_graph_maxit[which][pi] = maxit;
+            c->pcg_graph_launches[which][pi] = c->launches - l0;
+            c->launches = l0;
+            c->applies = a0;
+        }
+        gexec = slot;
+    }
+    for (;;) {
+        for (int k = 0; k < batch; k += 2) {
+            if (gexec) {
+                GM_CUDA_TRY(c, cudaGraphLaunch(gexec, s));
+                c->launches += c->pcg_graph_launches[which][pi];
+                c->applies += 2;
+            } else if ((rc = two_iterations(s))) {
+                return rc;
+            }
         }
         GM_CUDA_TRY(c, cudaMemcpyAsync(hs, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
         GM_CUDA_TRY(c, cudaStreamSynchronize(s));
@@ -90,6 +150,8 @@ int gm_pcg(gm_ctx* c, int which, int prec, const double* b, double* x, double rt
     }
     if (prec != GM_F64) {
         if ((rc = gm_launch_axpy_f2d(c, n, 1.0, (const float*)xx, x, s))) return rc;
+    } else {
+        if ((rc = gm_launch_axpby(c, n, 1.0, (const double*)xx, 1.0, x, s))) return rc;
     }
     if (iters) *iters = hs->it;
     if (relres) *relres = hs->rr0 > 0 ? std::sqrt(hs->rr / hs->rr0) : 0.0;
@@ -123,8 +185,9 @@ static int dot2(gm_ctx* c, long long n, const double* x, const double* y, const 
 int gm_prevost(gm_ctx* c, int prec, const double* b1, const double* b2, double* x1, double* x2,
                double outer_rtol, int outer_maxit, double inner_rtol, int inner_maxit,
                int* outer_it, long long* inner_k, long long* inner_a, double* relres,
-               cudaStream_t s)
+               cudaStream_t s, int schur_precond)
 {
+    const int pw = schur_precond == 1 ? 2 : 1;   // preconditioner operator
     const long long N = c->N, N3 = 3 * N;
     int rc, it_in;
     double* y1 = c->o_y1.as<double>();
@@ -138,16 +201,16 @@ int gm_prevost(gm_ctx* c, int prec, const double* b1, const double* b2, double* 
     double* t1 = c->o_t1.as<double>();
     long long ik = 0, ia = 0;
 
-    GM_CUDA_TRY(c, cudaMemsetAsync(y1, 0, N3 * sizeof(double), s));
-    if ((rc = gm_pcg(c, 0, prec, b1, y1, inner_rtol, inner_maxit, &it_in, nullptr, s))) return rc;
+    rc = gm_pcg(c, 0, prec, b1, y1, inner_rtol, inner_maxit, &it_in, nullptr, s, true);
+    if (rc && rc != GM_ENOCONV) return rc;
     ik += it_in;
     if ((rc = gm_launch_apply_f64(c, GM_MODE_AUP, 0, 0, 1, 0, 0, y1, nullptr, nullptr, t1, s, nullptr))) return rc;
     GM_CUDA_TRY(c, cudaMemcpyAsync(r, b2, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if ((rc = gm_launch_axpby(c, N, -1.0, t1, 1.0, r, s))) return rc;
     GM_CUDA_TRY(c, cudaMemsetAsync(x2, 0, N * sizeof(double), s));
     GM_CUDA_TRY(c, cudaMemcpyAsync(x1, y1, N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    GM_CUDA_TRY(c, cudaMemsetAsync(z, 0, N * sizeof(double), s));
-    if ((rc = gm_pcg(c, 1, prec, r, z, inner_rtol, inner_maxit, &it_in, nullptr, s))) return rc;
+    rc = gm_pcg(c, pw, prec, r, z, inner_rtol, inner_maxit, &it_in, nullptr, s, true);
+    if (rc && rc != GM_ENOCONV) return rc;
     ia += it_in;
     GM_CUDA_TRY(c, cudaMemcpyAsync(p, z, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     double d[2];
@@ -163,8 +226,8 @@ int gm_prevost(gm_ctx* c, int prec, const double* b1, const double* b2, double* 
         }
         // w = K_T^-1 A_pu p ;  q = A22 p + A_up w
         if ((rc = gm_launch_apply_f64(c, GM_MODE_APU, 0, 1, 0, 0, 0, nullptr, p, t3, nullptr, s, nullptr))) return rc;
-        GM_CUDA_TRY(c, cudaMemsetAsync(w, 0, N3 * sizeof(double), s));
-        if ((rc = gm_pcg(c, 0, prec, t3, w, inner_rtol, inner_maxit, &it_in, nullptr, s))) return rc;
+        rc = gm_pcg(c, 0, prec, t3, w, inner_rtol, inner_maxit, &it_in, nullptr, s, true);
+        if (rc && rc != GM_ENOCONV) return rc;
         ik += it_in;
         if ((rc = gm_launch_apply_f64(c, GM_MODE_A22, 0, 0, 0, 1, c->dt, nullptr, p, nullptr, q, s, nullptr))) return rc;
         if ((rc = gm_launch_apply_f64(c, GM_MODE_AUP, 0, 0, 1, 0, 0, w, nullptr, nullptr, t1, s, nullptr))) return rc;
@@ -177,8 +240,8 @@ int gm_prevost(gm_ctx* c, int prec, const double* b1, const double* b2, double* 
         if ((rc = gm_launch_axpby(c, N3, alpha, w, 1.0, x1, s))) return rc;
         if ((rc = gm_launch_axpby(c, N, -alpha, q, 1.0, r, s))) return rc;
         GM_CUDA_TRY(c, cudaMemcpyAsync(zold, z, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        GM_CUDA_TRY(c, cudaMemsetAsync(z, 0, N * sizeof(double), s));
-        if ((rc = gm_pcg(c, 1, prec, r, z, inner_rtol, inner_maxit, &it_in, nullptr, s))) return rc;
+        rc = gm_pcg(c, pw, prec, r, z, inner_rtol, inner_maxit, &it_in, nullptr, s, true);
+        if (rc && rc != GM_ENOCONV) return rc;
         ia += it_in;
         if ((rc = dot2(c, N, r, z, r, zold, d, s))) return rc;
         const double rz_new = d[0];

@@ -96,3 +96,45 @@ def test_fullsize_slipfront_step_properties():
     sig = row > 1e-6 * row[0]
     assert sig[:3].all() and np.all(np.diff(row[sig]) < 0)
     assert row.min() > -1e-6 * row[0]
+
+
+def test_fullsize_slip_front_matches_closed_form():
+    """The 64^3 slip-front workload run through its 50-step schedule on the GPU
+    (FP32-refined, Newton 1e-8): the pressure front L(t) (where p = dp* E1(1))
+    and the rupture radius R(t) (farthest slipping pair) agree with
+    L = sqrt(4 D t), R = lambda(T) L (Sec. 4.2) within the paper's bounds
+    (8 % for L, 5 % for R) once the fronts span several cells (t > 1000 s)."""
+    import math
+    from oracle import analytic as A
+    need_gpu()
+    n = 64
+    prob = W.slip_front(n=n)
+    s = solver_for(prob)
+    fp = prob.fault
+    D = A.fault_diffusivity(fp.wk_par, fp.MF, prob.mu_f, fp.w0)
+    dps = A.theis_dpstar(prob.fp.sum(), prob.mu_f, fp.wk_par)
+    lam = A.lambda_of_T(0.1)
+    h = prob.h[0]
+    x = (np.arange(n + 1) - n // 2) * h
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    r = np.sqrt(X ** 2 + Y ** 2).ravel()
+    nb = (n + 1) ** 2
+    t = 0.0
+    checked = 0
+    for k, dt in enumerate(prob.dts):
+        s.step(dt, newton_rtol=1e-8, precision=1)
+        t += dt
+        if t < 1000.0:
+            continue
+        st = s.get_state()
+        p = st["p"][prob.kf * nb:(prob.kf + 1) * nb]
+        row = p.reshape(n + 1, n + 1)[n // 2, n // 2:]
+        target = dps * 0.21938393439552          # E1(1)
+        i = int(np.where(row < target)[0][0])
+        L = h * (i - 1 + (row[i - 1] - target) / (row[i - 1] - row[i]))
+        R = r[st["flags"] == 2].max()
+        La = math.sqrt(4 * D * t)
+        assert abs(L - La) / La < 0.08, (t, L, La)
+        assert abs(R - lam * La) / (lam * La) < 0.05, (t, R, lam * La)
+        checked += 1
+    assert checked >= 5

@@ -190,9 +190,11 @@ def test_prevost_vs_direct(name):
     assert rep["iterations"] >= 1
 
 
-@pytest.mark.parametrize("name,steps", [("box_tied_8", 5), ("sheared_x_untied", 2),
-                                        ("ragged_tied", 2), ("no_fault", 3)])
-def test_implicit_steps(name, steps):
+@pytest.mark.parametrize("name,steps,sp", [("box_tied_8", 5, 0), ("sheared_x_untied", 2, 0),
+                                           ("ragged_tied", 2, 0), ("no_fault", 3, 0),
+                                           ("box_tied_8", 5, 1), ("sheared_x_untied", 2, 1)])
+def test_implicit_steps(name, steps, sp):
+    """sp = 1 uses the fixed-stress Schur preconditioner: same converged result."""
     prob = CASES[name]()
     if name == "ragged_tied":
         prob.fp = prob.fp * 20
@@ -200,7 +202,7 @@ def test_implicit_steps(name, steps):
     s = solver_for(prob)
     model, ref = osolve.run(prob, nsteps=steps, rtol=1e-12)
     for k in range(steps):
-        rep = s.step(prob.dts[k], newton_rtol=1e-12)
+        rep = s.step(prob.dts[k], newton_rtol=1e-12, schur_precond=sp)
         st = s.get_state()
         r = ref[k]
         assert rel(st["u"], r.u) < 1e-9, (k, rel(st["u"], r.u))
@@ -225,3 +227,20 @@ def test_state_roundtrip():
     b = s2.get_state()
     for k in ("u", "p", "dlie", "flags", "slip"):
         assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("name,steps", [("box_tied_8", 5), ("sheared_x_untied", 2)])
+def test_implicit_steps_fp32_refined(name, steps):
+    """FP32 operators and preconditioners inside the FP64 Newton / refinement loop:
+    fields within 1e-8 of the FP64 oracle and identical fault states."""
+    prob = CASES[name]()
+    need_gpu()
+    s = solver_for(prob)
+    model, ref = osolve.run(prob, nsteps=steps, rtol=1e-12)
+    for k in range(steps):
+        s.step(prob.dts[k], newton_rtol=1e-12, precision=1)
+        st = s.get_state()
+        r = ref[k]
+        assert rel(st["u"], r.u) < 1e-8, (k, rel(st["u"], r.u))
+        assert rel(st["p"], r.p) < 1e-8, (k, rel(st["p"], r.p))
+        assert np.array_equal(st["flags"].astype(np.int64), r.flags), k
