@@ -225,6 +225,35 @@ int gm_residual_noalloc(gm_ctx* ctx, const double* du_dev, const double* dp_dev,
 int gm_partitioned_step(gm_ctx* ctx, double dt, const gm_step_opts* opts_host,
                         gm_step_report* report_host, void* stream);
 
+/* ---- parameters and adjoint (gradients) ------------------ */
+
+/* Replace the element permeabilities (n = n_el, or 1 to broadcast) without
+ * resetting the state; diagonals are refreshed.  Synchronises. */
+int gm_set_permeability(gm_ctx* ctx, const double* k_host, int64_t n);
+
+/* Friction coefficient of the fault (Eq. yield_function): n = 1 sets the common
+ * value, n = pair count sets one value per pair.  Takes effect at the next
+ * return map.  Synchronises. */
+int gm_set_friction(gm_ctx* ctx, const double* f_host, int64_t n);
+
+/* Adjoint of the last converged implicit step (call it right after
+ * gm_partitioned_step, before anything re-runs the return map).  For an
+ * objective J(u, p) whose derivatives the caller gives as device vectors
+ * dJ_du (3N), dJ_dp (N) and dJ_dslip (2 per pair, field-major: derivative with
+ * respect to the slip P_t [[u]] in the fault frame) -- any may be NULL -- it
+ * solves (dF/dx)^T lambda = dJ/dx with the consistent Jacobian of the step
+ * (Sec. 3.3.1, fault states frozen, slipping pairs with the nonsymmetric
+ * tangent) by flexible GMRES preconditioned with the partitioned CG of
+ * Sec. 3.3.2, and returns dJ/dtheta = -lambda^T dF/dtheta for
+ *   g_logk_dev (n_el): theta = log k_e,   g_f_dev (pairs): theta = f_i,
+ *   g_logQ_host (scalar): theta = log of a common factor on the sources.
+ * The state before the step is held fixed.  rtol is the relative GMRES
+ * tolerance, maxit its iteration limit.  Synchronises. */
+int gm_adjoint_step(gm_ctx* ctx, const double* dJ_du_dev, const double* dJ_dp_dev,
+                    const double* dJ_dslip_dev, double* g_logk_dev, double* g_f_dev,
+                    double* g_logQ_host, double rtol, int maxit, gm_solve_report* report_host,
+                    void* stream);
+
 /* ---- state I/O (checkpoint / resume) --------------------------------- */
 
 /* Copy the accepted state to host arrays (any may be NULL): u (3N), p (N, tied

@@ -85,6 +85,10 @@ _SIG = {
     "gm_state_device": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P)]),
     "gm_sizes": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "gm_counters": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "gm_set_permeability": (C.c_int, [_P, _D, C.c_int64]),
+    "gm_set_friction": (C.c_int, [_P, _D, C.c_int64]),
+    "gm_adjoint_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _D, C.c_double, C.c_int,
+                                  C.POINTER(SolveReport), _P]),
 }
 
 _lib = None
@@ -318,6 +322,32 @@ class Solver:
                                        None if d is None else _dptr(d),
                                        None if f is None else f.ctypes.data_as(C.POINTER(C.c_int8))))
 
+    def set_permeability(self, k):
+        """Element permeabilities (n_el values or one), state kept."""
+        a = np.ascontiguousarray(np.atleast_1d(k), np.float64)
+        self._chk(self._L.gm_set_permeability(self.h, _dptr(a), a.size))
+
+    def set_friction(self, f):
+        """Friction coefficient: one value or one per fault pair."""
+        a = np.ascontiguousarray(np.atleast_1d(f), np.float64)
+        self._chk(self._L.gm_set_friction(self.h, _dptr(a), a.size))
+
+    def adjoint(self, dJ_du=None, dJ_dp=None, dJ_dslip=None, rtol=1e-10, maxit=300, stream=None):
+        """gm_adjoint_step for the last converged step.  Inputs are CUDA
+        float64 tensors shaped (3, N), (N,), (2, P) or None.  Returns
+        (g_logk (n_el,), g_f (P,), g_logQ float, report)."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        gk = torch.empty(self.n_el, dtype=torch.float64, device=dev)
+        gf = torch.zeros(max(self.P, 1), dtype=torch.float64, device=dev)
+        gq = C.c_double()
+        rep = SolveReport()
+        keep = [t.contiguous() if t is not None else None for t in (dJ_du, dJ_dp, dJ_dslip)]
+        ptr = [None if t is None else _tptr(t) for t in keep]
+        self._chk(self._L.gm_adjoint_step(self.h, ptr[0], ptr[1], ptr[2], _tptr(gk), _tptr(gf),
+                                          C.byref(gq), rtol, maxit, C.byref(rep), _stream_ptr(stream)))
+        return gk, gf[:self.P], gq.value, dict(iterations=rep.iterations, rel_residual=rep.rel_residual)
+
     def counters(self):
         """(kernel launches, bulk operator applies) since bind."""
         a, b = C.c_int64(), C.c_int64()
@@ -329,3 +359,36 @@ class Solver:
         u, p = _P(), _P()
         self._chk(self._L.gm_state_device(self.h, C.byref(u), C.byref(p)))
         return u.value, p.value
+
+
+def implicit_step_fn():
+    """torch.autograd.Function for one implicit step as a function of the
+    element log-permeabilities, the friction coefficient and the log scaling
+    of the fluid sources.  forward(logk, f, logQ, solver, dt, (fu, fp_base), kw)
+    runs gm_partitioned_step from the solver's current state and returns
+    (slip (2, P), p (N,)); backward calls gm_adjoint_step.  The solver's state
+    advances in forward; restore it with set_state to re-evaluate."""
+    import torch
+
+    class ImplicitStep(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, logk, f, logQ, solver, dt, loads, kw):
+            fu, fp_base = loads
+            solver.set_permeability(torch.exp(logk.detach()).cpu().numpy())
+            solver.set_friction(np.array([float(f)]))
+            solver.loads(fu, np.asarray(fp_base) * float(torch.exp(logQ.detach())))
+            solver.step(dt, **(kw or {}))
+            st = solver.get_state()
+            dev = torch.device("cuda", solver.device)
+            ctx.solver = solver
+            return (torch.as_tensor(st["slip"], device=dev), torch.as_tensor(st["p"], device=dev))
+
+        @staticmethod
+        def backward(ctx, g_slip, g_p):
+            s = ctx.solver
+            gk, gf, gq, _ = s.adjoint(dJ_dp=g_p.to(torch.float64).contiguous(),
+                                      dJ_dslip=g_slip.to(torch.float64).contiguous())
+            return (gk, gf.sum(), torch.tensor(gq, dtype=torch.float64, device=gk.device),
+                    None, None, None, None)
+
+    return ImplicitStep

@@ -1,0 +1,331 @@
+// Adjoint of the last converged implicit step, and the parameter set-up calls
+// it needs (per-element permeability, per-pair friction without a rebind).
+//
+// For the converged step F(x; theta) = 0 (Sec. 3.3.1, residuals of Eq.
+// nonlinear_system, x = (u, p) at the end of the step, previous state fixed) and
+// an objective J(x):  dJ/dtheta = -lambda^T dF/dtheta  with
+// (dF/dx)^T lambda = (dJ/dx)^T on the free dofs.  dF/dx is the consistent
+// Jacobian with the fault states frozen; for slipping pairs its cohesive block
+// is the symmetric Newton tangent minus f k_n tau n^T (Sec. 2.2.1, Eq. corrector
+// differentiated at fixed state).  The transposed system
+//     [K_b + K_coh^T   A_pu ] [l_u]   [g_u]
+//     [   -A_up        A22  ] [l_p] = [g_p]
+// is solved by flexible GMRES, right-preconditioned by Prevost's partitioned CG
+// on the symmetric Newton Jacobian (Sec. 3.3.2) applied to (r_u, -r_p), whose
+// p-part is negated back.
+//   d F_f / d log k_e = dt (k_e/mu) L_e p_e        -> g_logk[e] = -dt l_p,e . (k_e/mu) L_e p_e
+//   d F_m / d f_i     = +- A_i t'_n tau  (slipping) -> g_f[i] = -A_i t'_n tau . [[l_u]]_i
+//   d F_f / d log Q   = -dt f^p                     -> g_logQ = dt l_p . f^p
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "gm_internal.cuh"
+
+namespace {
+
+// g = dJ/dx on the free dofs: dJ/du, plus the lip terms of dJ/dslip
+// (slip = P_t [[u]] in the fault frame), plus dJ/dp folded onto tied masters.
+__global__ void adj_rhs_kernel(GridDesc g, const double* dJu, const double* dJp, const double* dJs,
+                               const uint8_t* mask, double t1x, double t1y, double t1z, double t2x,
+                               double t2y, double t2z, double* out)
+{
+    const long long N = g.N;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const unsigned m = mask[n];
+    const long long kk = n / g.nb, pid = n - kk * g.nb;
+    double gu[3] = {0, 0, 0};
+    if (dJu)
+        for (int c = 0; c < 3; ++c) gu[c] = dJu[c * N + n];
+    if (dJs && g.kf >= 0 && (kk == g.kf || kk == g.kf + 1)) {
+        const double sg = kk == g.kf + 1 ? 1.0 : -1.0;
+        const long long P = g.nb;
+        const double a = dJs[pid], b = dJs[P + pid];
+        gu[0] += sg * (a * t1x + b * t2x);
+        gu[1] += sg * (a * t1y + b * t2y);
+        gu[2] += sg * (a * t1z + b * t2z);
+    }
+    for (int c = 0; c < 3; ++c) out[c * N + n] = ((m >> c) & 1u) ? 0.0 : gu[c];
+    double gp = dJp ? dJp[n] : 0.0;
+    const bool slave = g.tied && kk == g.kf + 1;
+    if (g.tied && kk == g.kf && dJp) gp += dJp[n + g.nb];
+    out[3 * N + n] = (slave || ((m >> 3) & 1u)) ? 0.0 : gp;
+}
+
+__global__ void adj_flip_p_kernel(long long N, const double* in, double* out)
+{
+    // out = (in_u, -in_p)
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 4 * N;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = i < 3 * N ? in[i] : -in[i];
+}
+
+struct GradArgs {
+    GridDesc g;
+    const double* lp;    // lambda_p (N)
+    const double* p;     // accepted pressure (N)
+    const double* kap;   // k/mu per element
+    double L[64];
+    double dt;
+    double* gk;          // per element
+};
+
+__global__ void adj_grad_logk_kernel(const GradArgs a)
+{
+    const long long nel = (long long)a.g.nx * a.g.ny * a.g.nz;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nel) return;
+    const int ei = (int)(e % a.g.nx), ej = (int)((e / a.g.nx) % a.g.ny), ek = (int)(e / ((long long)a.g.nx * a.g.ny));
+    const int kb = ek + ((a.g.kf >= 0 && ek >= a.g.kf) ? 1 : 0);
+    double lv[8], pv[8];
+    for (int loc = 0; loc < 8; ++loc) {
+        const int ax = loc & 1, ay = (loc >> 1) & 1, az = (loc >> 2) & 1;
+        long long node = (ei + ax) + (long long)(a.g.nx + 1) * ((ej + ay) + (long long)(a.g.ny + 1) * (kb + az));
+        if (a.g.tied && kb + az == a.g.kf + 1) node -= a.g.nb;   // slave lip -> master dof
+        lv[loc] = a.lp[node];
+        pv[loc] = a.p[node];
+    }
+    double s = 0.0;
+    for (int i = 0; i < 8; ++i) {
+        double t = 0.0;
+        for (int j = 0; j < 8; ++j) t += a.L[8 * i + j] * pv[j];
+        s += lv[i] * t;
+    }
+    a.gk[e] = -a.dt * a.kap[e] * s;
+}
+
+__global__ void adj_grad_f_kernel(GridDesc g, const double* lu, const double* tn, const double* tauc,
+                                  double Aq, double* gf)
+{
+    const long long P = g.nb;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const long long N = g.N;
+    const long long nm = i + g.nb * g.kf, np = nm + g.nb;
+    if (tauc[3 * P + i] == 0.0) { gf[i] = 0.0; return; }
+    const int pi = (int)(i % (g.nx + 1)), pj = (int)(i / (g.nx + 1));
+    const int nqi = (pi > 0) + (pi < g.nx), nqj = (pj > 0) + (pj < g.ny);
+    const double Ai = Aq * 0.25 * nqi * nqj;
+    double d = 0.0;
+    for (int c = 0; c < 3; ++c) d += tauc[c * P + i] * (lu[c * N + np] - lu[c * N + nm]);
+    gf[i] = -Ai * tn[i] * d;
+}
+
+int ensure_adjoint_buffers(gm_ctx* c, int m)
+{
+    if (c->adj_m >= m) return GM_OK;
+    const size_t v = (size_t)4 * c->N * sizeof(double);
+    cudaError_t e;
+    if ((e = c->adj_V.alloc(v * (m + 1))) != cudaSuccess ||
+        (e = c->adj_Z.alloc(v * m)) != cudaSuccess || (e = c->adj_w.alloc(v)) != cudaSuccess ||
+        (e = c->adj_b.alloc(v)) != cudaSuccess || (e = c->adj_x.alloc(v)) != cudaSuccess ||
+        (e = c->adj_t.alloc(v)) != cudaSuccess)
+        return c->set_err(GM_ENOMEM, std::string("adjoint: cudaMalloc: ") + cudaGetErrorString(e));
+    c->adj_m = m;
+    return GM_OK;
+}
+
+int dot(gm_ctx* c, long long n, const double* x, const double* y, double* out, cudaStream_t s)
+{
+    double* d = reinterpret_cast<double*>(c->dscal.as<PcgScalars>() + 7);
+    int rc = gm_launch_dot(c, n, x, y, nullptr, nullptr, d, s);
+    if (rc) return rc;
+    double* h = reinterpret_cast<double*>(static_cast<char*>(c->hpin) + 3584);
+    GM_CUDA_TRY(c, cudaMemcpyAsync(h, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    GM_CUDA_TRY(c, cudaStreamSynchronize(s));
+    *out = h[0];
+    return GM_OK;
+}
+
+// y = J_cons^T x (free dofs)
+int apply_adjoint_operator(gm_ctx* c, const double* x, double* y, cudaStream_t s)
+{
+    const long long N = c->N;
+    c->fault_cons = 2;
+    const int rc = gm_launch_apply_f64(c, GM_MODE_J, 1, 1, -1, 1, c->dt, x, x + 3 * N, y, y + 3 * N, s, nullptr);
+    c->fault_cons = 0;
+    return rc;
+}
+
+// z = flip(Prevost_sym(flip(v)))
+int apply_preconditioner(gm_ctx* c, const double* v, double* z, double prtol, int pmaxit,
+                         cudaStream_t s, long long* inner_k)
+{
+    const long long N = c->N;
+    double* t = c->adj_t.as<double>();
+    adj_flip_p_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(N, v, t);
+    GM_LAUNCHED(c);
+    int oit = 0;
+    long long ia = 0;
+    double rr = 0;
+    int rc = gm_prevost(c, GM_F64, t, t + 3 * N, z, z + 3 * N, prtol, pmaxit, prtol * 1e-2, 20000, &oit,
+                        inner_k, &ia, &rr, s, 0);
+    if (rc && rc != GM_ENOCONV) return rc;
+    adj_flip_p_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(N, z, z);
+    GM_LAUNCHED(c);
+    return GM_OK;
+}
+
+}  // namespace
+
+extern "C" int gm_set_permeability(gm_ctx* c, const double* k, int64_t n)
+{
+    if (!c) return GM_EINVAL;
+    if (!c->bound) return c->set_err(GM_ESTATE, "set_permeability: not bound");
+    if (!k || (n != 1 && n != c->n_el)) return c->set_err(GM_EINVAL, "set_permeability: n must be 1 or n_el");
+    for (long long e = 0; e < c->n_el; ++e) {
+        const double v = k[n == 1 ? 0 : e];
+        if (!(v >= 0)) return c->set_err(GM_EINVAL, "set_permeability: k >= 0");
+        c->kperm[e] = v;
+    }
+    return gm_upload_permeability(c);
+}
+
+extern "C" int gm_set_friction(gm_ctx* c, const double* f, int64_t n)
+{
+    if (!c) return GM_EINVAL;
+    if (!c->bound || !c->has_fault) return c->set_err(GM_ESTATE, "set_friction: needs a bound fault");
+    if (!f || (n != 1 && n != c->P)) return c->set_err(GM_EINVAL, "set_friction: n must be 1 or the pair count");
+    if (n == 1) {
+        if (!(f[0] >= 0)) return c->set_err(GM_EINVAL, "set_friction: f >= 0");
+        c->fp.f = f[0];
+        c->has_fpair = false;
+        return GM_OK;
+    }
+    for (long long i = 0; i < n; ++i)
+        if (!(f[i] >= 0)) return c->set_err(GM_EINVAL, "set_friction: f >= 0");
+    GM_CUDA_TRY(c, cudaMemcpy(c->dfpair.p, f, n * sizeof(double), cudaMemcpyHostToDevice));
+    c->has_fpair = true;
+    return GM_OK;
+}
+
+extern "C" int gm_adjoint_step(gm_ctx* c, const double* dJ_du, const double* dJ_dp, const double* dJ_dslip,
+                               double* g_logk, double* g_f, double* g_logQ, double rtol, int maxit,
+                               gm_solve_report* rep, void* stream)
+{
+    if (!c) return GM_EINVAL;
+    if (!c->bound) return c->set_err(GM_ESTATE, "adjoint: not bound");
+    if (!(rtol > 0) || maxit < 1) return c->set_err(GM_EINVAL, "adjoint: bad tolerance or maxit");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long N = c->N, n4 = 4 * N;
+    const int m = 30;
+    int rc = ensure_adjoint_buffers(c, m);
+    if (rc) return rc;
+    double* V = c->adj_V.as<double>();
+    double* Z = c->adj_Z.as<double>();
+    double* w = c->adj_w.as<double>();
+    double* b = c->adj_b.as<double>();
+    double* x = c->adj_x.as<double>();
+    const int nb = (int)((N + 255) / 256);
+    adj_rhs_kernel<<<nb, 256, 0, s>>>(c->g, dJ_du, dJ_dp, dJ_dslip, c->dmask.as<uint8_t>(), c->t1[0],
+                                      c->t1[1], c->t1[2], c->t2[0], c->t2[1], c->t2[2], b);
+    GM_LAUNCHED(c);
+    if ((rc = gm_launch_block_jacobi(c, s))) return rc;   // symmetric Newton tangent of the frozen state
+    GM_CUDA_TRY(c, cudaMemsetAsync(x, 0, n4 * sizeof(double), s));
+    double beta0;
+    if ((rc = dot(c, n4, b, b, &beta0, s))) return rc;
+    beta0 = std::sqrt(beta0);
+    long long ik = 0;
+    int it = 0;
+    double res = beta0;
+    const double prtol = 1e-8;
+    // flexible GMRES(m), right preconditioned; restart from r = b - A x
+    while (beta0 > 0 && res > rtol * beta0 && it < maxit) {
+        double* r = V;   // V[0]
+        if ((rc = apply_adjoint_operator(c, x, w, s))) return rc;
+        GM_CUDA_TRY(c, cudaMemcpyAsync(r, b, n4 * 8, cudaMemcpyDeviceToDevice, s));
+        if ((rc = gm_launch_axpby(c, n4, -1.0, w, 1.0, r, s))) return rc;
+        double beta;
+        if ((rc = dot(c, n4, r, r, &beta, s))) return rc;
+        beta = std::sqrt(beta);
+        res = beta;
+        if (!(beta > rtol * beta0)) break;
+        if ((rc = gm_launch_axpby(c, n4, 1.0 / beta, r, 0.0, r, s))) return rc;
+        std::vector<double> H((m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), gv(m + 1, 0.0);
+        gv[0] = beta;
+        int j;
+        for (j = 0; j < m && it < maxit; ++j, ++it) {
+            double* vj = V + (size_t)j * n4;
+            double* zj = Z + (size_t)j * n4;
+            if ((rc = apply_preconditioner(c, vj, zj, prtol, 500, s, &ik))) return rc;
+            if ((rc = apply_adjoint_operator(c, zj, w, s))) return rc;
+            for (int i = 0; i <= j; ++i) {
+                double h;
+                if ((rc = dot(c, n4, w, V + (size_t)i * n4, &h, s))) return rc;
+                H[i * m + j] = h;
+                if ((rc = gm_launch_axpby(c, n4, -h, V + (size_t)i * n4, 1.0, w, s))) return rc;
+            }
+            double hn;
+            if ((rc = dot(c, n4, w, w, &hn, s))) return rc;
+            hn = std::sqrt(hn);
+            H[(j + 1) * m + j] = hn;
+            if (hn > 0)
+                if ((rc = gm_launch_axpby(c, n4, 1.0 / hn, w, 0.0, V + (size_t)(j + 1) * n4, s))) return rc;
+            for (int i = 0; i < j; ++i) {
+                const double a = H[i * m + j], bb = H[(i + 1) * m + j];
+                H[i * m + j] = cs[i] * a + sn[i] * bb;
+                H[(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+            }
+            const double a = H[j * m + j], bb = H[(j + 1) * m + j];
+            const double rr = std::sqrt(a * a + bb * bb);
+            cs[j] = rr > 0 ? a / rr : 1.0;
+            sn[j] = rr > 0 ? bb / rr : 0.0;
+            H[j * m + j] = rr;
+            H[(j + 1) * m + j] = 0.0;
+            gv[j + 1] = -sn[j] * gv[j];
+            gv[j] = cs[j] * gv[j];
+            res = std::fabs(gv[j + 1]);
+            if (!std::isfinite(res)) return c->set_err(GM_ENAN, "adjoint: non-finite GMRES residual");
+            if (res <= rtol * beta0 || hn == 0) { ++j; ++it; break; }
+        }
+        // x += Z y,  H y = g (upper triangular j x j)
+        std::vector<double> y(j, 0.0);
+        for (int i = j - 1; i >= 0; --i) {
+            double t = gv[i];
+            for (int k = i + 1; k < j; ++k) t -= H[i * m + k] * y[k];
+            y[i] = t / H[i * m + i];
+        }
+        for (int i = 0; i < j; ++i)
+            if ((rc = gm_launch_axpby(c, n4, y[i], Z + (size_t)i * n4, 1.0, x, s))) return rc;
+    }
+    // true residual
+    if ((rc = apply_adjoint_operator(c, x, w, s))) return rc;
+    if ((rc = gm_launch_axpby(c, n4, 1.0, b, -1.0, w, s))) return rc;
+    double rfin;
+    if ((rc = dot(c, n4, w, w, &rfin, s))) return rc;
+    rfin = std::sqrt(rfin);
+    if (rep) {
+        rep->iterations = it;
+        rep->rel_residual = beta0 > 0 ? rfin / beta0 : 0.0;
+        rep->status = GM_OK;
+    }
+    const double* lu = x;
+    const double* lp = x + 3 * N;
+    if (g_logk) {
+        GradArgs ga;
+        ga.g = c->g;
+        ga.lp = lp;
+        ga.p = c->dp_n.as<double>();
+        ga.kap = c->dK64.as<double>();
+        for (int q = 0; q < 64; ++q) ga.L[q] = c->Lref[q];
+        ga.dt = c->dt;
+        ga.gk = g_logk;
+        adj_grad_logk_kernel<<<(int)((c->n_el + 255) / 256), 256, 0, s>>>(ga);
+        GM_LAUNCHED(c);
+    }
+    if (g_f && c->has_fault) {
+        adj_grad_f_kernel<<<(int)((c->P + 255) / 256), 256, 0, s>>>(c->g, lu, c->dtn.as<double>(),
+                                                                     c->dtauc.as<double>(), c->Aq, g_f);
+        GM_LAUNCHED(c);
+    }
+    if (g_logQ) {
+        double d;
+        if ((rc = dot(c, N, lp, c->dfp.as<double>(), &d, s))) return rc;
+        *g_logQ = c->dt * d;
+    }
+    GM_CUDA_TRY(c, cudaStreamSynchronize(s));
+    if (beta0 > 0 && rfin > 10 * rtol * beta0)
+        return c->set_err(GM_ENOCONV, "adjoint: GMRES did not reach the tolerance (" + std::to_string(rfin / beta0) + ")");
+    return GM_OK;
+}

@@ -105,6 +105,17 @@ gm_fault_apply_kernel(const FaultArgs<T> a)
                 f[0] = s * (d00 * jmp[0] + d01 * jmp[1] + d02 * jmp[2]);
                 f[1] = s * (d01 * jmp[0] + d11 * jmp[1] + d12 * jmp[2]);
                 f[2] = s * (d02 * jmp[0] + d12 * jmp[1] + d22 * jmp[2]);
+                if (a.cons != 0) {
+                    const T co = (T)a.tauc[3 * P + i];
+                    if (co != T(0)) {
+                        const T tg[3] = {(T)a.tauc[i], (T)a.tauc[P + i], (T)a.tauc[2 * P + i]};
+                        const T* v = a.cons == 1 ? tg : a.n;      // left vector
+                        const T* w = a.cons == 1 ? a.n : tg;      // right vector
+                        const T sc = s * co * (w[0] * jmp[0] + w[1] * jmp[1] + w[2] * jmp[2]);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) f[c] = fma(sc, v[c], f[c]);
+                    }
+                }
             }
             if constexpr (DO_APU) {
                 const T s = a.cApu * Ai * p_av;
@@ -238,6 +249,8 @@ inline FaultArgs<T> gm_fault_args(gm_ctx* c, double cK, double cApu, double cAup
     for (int q = 0; q < 16; ++q) f.Lf[q] = T(c->Lf[q]);
     f.mask = c->dmask.as<uint8_t>();
     f.skip = nullptr;
+    f.tauc = c->dtauc.as<double>();
+    f.cons = c->fault_cons;
     f.part = nullptr;
     f.nbulk = 0;
     f.counter = nullptr;

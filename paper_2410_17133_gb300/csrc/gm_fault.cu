@@ -152,6 +152,14 @@ __global__ void gm_return_map_kernel(const LawArgs a)
         a.D64[q * P + i] = D[q];
         if (a.D32) a.D32[q * P + i] = (float)D[q];
     }
+    // consistent tangent of a slipping pair = D - f k_n tau n^T (frozen state)
+    const double tgx = tau1 * a.t1[0] + tau2 * a.t2[0];
+    const double tgy = tau1 * a.t1[1] + tau2 * a.t2[1];
+    const double tgz = tau1 * a.t1[2] + tau2 * a.t2[2];
+    a.tauc[i] = tgx;
+    a.tauc[P + i] = tgy;
+    a.tauc[2 * P + i] = tgz;
+    a.tauc[3 * P + i] = slip ? -fr * a.kn : 0.0;
 }
 
 int gm_launch_return_map(gm_ctx* c, const double* un, const double* du, cudaStream_t s)
@@ -162,7 +170,8 @@ int gm_launch_return_map(gm_ctx* c, const double* un, const double* du, cudaStre
     a.un = un;
     a.du = du;
     a.dlie_prev = c->ddlie_n.as<double>();
-    a.fpair = nullptr;
+    a.fpair = c->has_fpair ? c->dfpair.as<double>() : nullptr;
+    a.tauc = c->dtauc.as<double>();
     a.kn = c->fp.kn; a.ks = c->fp.ks; a.f = c->fp.f; a.tn0 = c->fp.tn0;
     a.tau0[0] = c->fp.tau0[0]; a.tau0[1] = c->fp.tau0[1];
     for (int d = 0; d < 3; ++d) { a.n[d] = c->nrm[d]; a.t1[d] = c->t1[d]; a.t2[d] = c->t2[d]; }

@@ -212,6 +212,24 @@ int bind_impl(gm_ctx* c);
 
 }  // namespace
 
+// per-element k/mu arrays (FP64, FP32) and the diagonals that depend on them
+int gm_upload_permeability(gm_ctx* c)
+{
+    const long long nel = c->n_el;
+    std::vector<double> kap(nel);
+    std::vector<float> f32(nel);
+    for (long long e = 0; e < nel; ++e) {
+        kap[e] = c->kperm[e] / c->mu_f;
+        f32[e] = (float)kap[e];
+    }
+    GM_CUDA_TRY(c, cudaMemcpy(c->dK64.p, kap.data(), nel * 8, cudaMemcpyHostToDevice));
+    GM_CUDA_TRY(c, cudaMemcpy(c->dK32.p, f32.data(), nel * 4, cudaMemcpyHostToDevice));
+    int rc = gm_launch_diag(c, 0);
+    if (rc) return rc;
+    GM_CUDA_TRY(c, cudaDeviceSynchronize());
+    return GM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -740,6 +758,12 @@ int bind_impl(gm_ctx* c)
                                     : pack_ref<GM_CLS_GEN>(K, A, M, L, c->R64);
     if (!ok) return c->set_err(GM_EINVAL, "bind: cell operators break the expected symmetry");
     cast_ref(c->R64, c->R32);
+    for (int a = 0; a < 8; ++a)
+        for (int b = 0; b < 8; ++b) c->Lref[8 * a + b] = L[a][b];
+    c->has_fpair = false;
+    c->fault_cons = 0;
+    c->adj_m = 0;
+    for (DevBuf* bf : {&c->adj_V, &c->adj_Z, &c->adj_w, &c->adj_b, &c->adj_x, &c->adj_t}) bf->release();
     for (int a = 0; a < 8; ++a) {
         for (int x = 0; x < 3; ++x)
             for (int y = 0; y < 3; ++y) c->Kblk_ref[a][3 * x + y] = K[3 * a + x][3 * a + y];
@@ -810,6 +834,7 @@ int bind_impl(gm_ctx* c)
         {&c->dts, (size_t)2 * P * 8}, {&c->ddlie, (size_t)2 * P * 8}, {&c->dT, (size_t)3 * P * 8},
         {&c->dF, (size_t)P * 8}, {&c->ddn, (size_t)P * 8}, {&c->dgs, (size_t)2 * P * 8},
         {&c->dD64, (size_t)6 * P * 8}, {&c->dD32, (size_t)6 * P * 4},
+        {&c->dtauc, (size_t)4 * P * 8}, {&c->dfpair, (size_t)P * 8},
         {&c->ddiagK, (size_t)N3 * 8}, {&c->ddiagA, (size_t)N * 8},
         {&c->dKinv64, (size_t)12 * N * 8}, {&c->dKinv32, (size_t)6 * N * 4},
         {&c->dAinv64, (size_t)N * 8}, {&c->dAinv32, (size_t)N * 4},
@@ -840,14 +865,16 @@ int bind_impl(gm_ctx* c)
     }
     // upload
     std::vector<float> f32(nel);
-    std::vector<double> kap(nel);
-    for (long long e = 0; e < nel; ++e) kap[e] = c->kperm[e] / c->mu_f;
     GM_CUDA_TRY(c, cudaMemcpy(c->dE64.p, c->E.data(), nel * 8, cudaMemcpyHostToDevice));
-    GM_CUDA_TRY(c, cudaMemcpy(c->dK64.p, kap.data(), nel * 8, cudaMemcpyHostToDevice));
     for (long long e = 0; e < nel; ++e) f32[e] = (float)c->E[e];
     GM_CUDA_TRY(c, cudaMemcpy(c->dE32.p, f32.data(), nel * 4, cudaMemcpyHostToDevice));
-    for (long long e = 0; e < nel; ++e) f32[e] = (float)kap[e];
-    GM_CUDA_TRY(c, cudaMemcpy(c->dK32.p, f32.data(), nel * 4, cudaMemcpyHostToDevice));
+    {
+        std::vector<double> kap(nel);
+        for (long long e = 0; e < nel; ++e) kap[e] = c->kperm[e] / c->mu_f;
+        GM_CUDA_TRY(c, cudaMemcpy(c->dK64.p, kap.data(), nel * 8, cudaMemcpyHostToDevice));
+        for (long long e = 0; e < nel; ++e) f32[e] = (float)kap[e];
+        GM_CUDA_TRY(c, cudaMemcpy(c->dK32.p, f32.data(), nel * 4, cudaMemcpyHostToDevice));
+    }
     // fixed-stress storage coefficient alpha^2 / K_dr with the drained bulk
     // modulus K_dr = E / (3 (1 - 2 nu)) of each element
     {

@@ -162,6 +162,11 @@ struct FaultArgs {
     int nbulk;
     unsigned* counter;
     PcgScalars* sc;
+    // consistent-tangent term of slipping pairs, coef * tau n^T with
+    // tauc = (tau_x, tau_y, tau_z, coef) per pair (field-major, 4P):
+    // cons 0 ignores it, 1 adds it, 2 adds its transpose coef * n tau^T
+    const double* tauc;
+    int cons;
 };
 
 struct LawArgs {
@@ -183,6 +188,7 @@ struct LawArgs {
     double* gs;              // 2P (P_t [[u]] in the fault frame)
     double* D64;             // 6P
     float* D32;              // 6P (or null)
+    double* tauc;            // 4P: slip direction and -f k_n (0 unless slipping)
 };
 
 
@@ -248,6 +254,12 @@ struct gm_ctx {
     DevBuf dE64, dK64, dE32, dK32, dmask, dfu, dfp;
     DevBuf du_n, dp_n, ddlie_n, dflags_n;              // accepted state
     DevBuf dstate, dtn, dts, ddlie, dT, dF, ddn, dgs, dD64, dD32;   // fault work
+    DevBuf dtauc, dfpair;                              // consistent-tangent term, per-pair f
+    bool has_fpair = false;
+    int fault_cons = 0;                                // tangent variant used by the fault kernel
+    double Lref[64] = {};                              // nodal L of the reference cell (k/mu = 1)
+    DevBuf adj_V, adj_Z, adj_w, adj_b, adj_x, adj_t;   // adjoint (FGMRES) work, allocated on first use
+    int adj_m = 0;
     DevBuf ddiagK, ddiagA, dKinv64, dKinv32, dAinv64, dAinv32;
     DevBuf dFS64, dFS32, dAfsinv64, dAfsinv32;         // fixed-stress storage term
     DevBuf dscal;                                      // PcgScalars[4] + misc
@@ -314,6 +326,7 @@ int gm_launch_apply_f32(gm_ctx* c, int mode, double cK, double cApu, double cAup
 
 // Fault law, residual, preconditioners
 int gm_launch_return_map(gm_ctx* c, const double* un, const double* du, cudaStream_t s);
+int gm_upload_permeability(gm_ctx* c);                 // kap arrays + diagonals from c->kperm
 int gm_launch_residual(gm_ctx* c, const double* y1u, const double* y1p, const double* y2p,
                        const double* ut, const double* pt, double* b, cudaStream_t s,
                        double* out2 /* device: rhat^2, shat^2 */);

@@ -1,0 +1,133 @@
+"""Adjoint of the converged implicit step on the GPU: gradients w.r.t. element
+log-permeability, friction (per pair) and log source scaling match the oracle's
+assembled adjoint (consistent tangent, frozen fault states), central finite
+differences of GPU steps, and the torch.autograd wrapper."""
+import copy
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import adjoint as oadj, fem, solve as osolve
+
+from gpu_common import cuda, need_gpu, rel, solver_for, torch
+
+pytestmark = pytest.mark.gpu
+S0, P0 = 1e-6, 1e6
+
+
+def scenario():
+    prob = W.fault_small(n=6, Q=5e-5, steps=3)
+    rng = np.random.default_rng(5)
+    P = prob.n_pairs
+    obs_pairs = rng.choice(P, 12, replace=False)
+    obs_nodes = rng.choice(prob.n_nodes, 8, replace=False)
+    return prob, obs_pairs, obs_nodes
+
+
+def J_of(slip, p, obs_pairs, obs_nodes):
+    """slip (P, 2), p (N,)"""
+    return float(np.sum(slip[obs_pairs] ** 2) / S0 ** 2 + np.sum(p[obs_nodes]) / P0)
+
+
+def dJ(slip, obs_pairs, obs_nodes, N):
+    g_s = np.zeros_like(slip)
+    g_s[obs_pairs] = 2 * slip[obs_pairs] / S0 ** 2
+    g_p = np.zeros(N)
+    np.add.at(g_p, obs_nodes, 1.0 / P0)
+    return g_s, g_p
+
+
+@pytest.fixture(scope="module")
+def gpu_case():
+    need_gpu()
+    prob, obs_pairs, obs_nodes = scenario()
+    s = solver_for(prob)
+    for dt in prob.dts[:2]:
+        s.step(dt, newton_rtol=1e-12)
+    st2 = s.get_state()
+    s.step(prob.dts[2], newton_rtol=1e-12)
+    st3 = s.get_state()
+    g_s, g_p = dJ(st3["slip"].T, obs_pairs, obs_nodes, s.N)
+    gk, gf, gq, rep = s.adjoint(dJ_dp=cuda(g_p), dJ_dslip=cuda(g_s.T), rtol=1e-11)
+    return dict(prob=prob, s=s, st2=st2, st3=st3, gk=gk.cpu().numpy(), gf=gf.cpu().numpy(), gq=gq,
+                rep=rep, obs_pairs=obs_pairs, obs_nodes=obs_nodes, g_s=g_s, g_p=g_p)
+
+
+def test_adjoint_matches_oracle(gpu_case):
+    c = gpu_case
+    prob = c["prob"]
+    model = fem.Model(prob)
+    st = osolve.initial_state(model)
+    for dt in prob.dts[:2]:
+        osolve.implicit_step(model, st, dt, rtol=1e-13)
+    dlie_prev = st.dlie.copy()
+    res = osolve.implicit_step(model, st, prob.dts[2], rtol=1e-13)
+    assert np.array_equal(res.flags, c["st3"]["flags"].astype(np.int64))
+    assert (res.flags == 2).sum() >= 5
+    g_s, g_p = dJ(res.slip, c["obs_pairs"], c["obs_nodes"], model.N)
+    p_master = res.p.copy()
+    p_master[model.fg["pairs"][:, 1]] = 0.0
+    g = oadj.adjoint_of_last_step(model, res.u.reshape(-1), p_master, dlie_prev, prob.dts[2],
+                                  dJ_dp=g_p, dJ_dslip=g_s)
+    assert c["rep"]["rel_residual"] < 1e-9
+    assert rel(c["gk"], g["g_logk"]) < 1e-6
+    assert rel(c["gf"], g["g_f"]) < 1e-6
+    assert c["gq"] == pytest.approx(g["g_logQ"], rel=1e-6)
+
+
+def test_adjoint_log_source_scaling_vs_finite_differences(gpu_case):
+    c = gpu_case
+    prob, s = c["prob"], c["s"]
+    h = 1e-4
+    Js = []
+    for sgn in (1, -1):
+        s.set_state(u=c["st2"]["u"], p=c["st2"]["p"], dlie=c["st2"]["dlie"], flags=c["st2"]["flags"])
+        s.loads(prob.fu, prob.fp * math.exp(sgn * h))
+        s.step(prob.dts[2], newton_rtol=1e-12)
+        st = s.get_state()
+        Js.append(J_of(st["slip"].T, st["p"], c["obs_pairs"], c["obs_nodes"]))
+    s.loads(prob.fu, prob.fp)
+    fd = (Js[0] - Js[1]) / (2 * h)
+    assert c["gq"] == pytest.approx(fd, rel=1e-5)
+
+
+def test_adjoint_friction_vs_finite_differences(gpu_case):
+    c = gpu_case
+    prob, s = c["prob"], c["s"]
+    h = 1e-6
+    Js = []
+    for sgn in (1, -1):
+        s.set_state(u=c["st2"]["u"], p=c["st2"]["p"], dlie=c["st2"]["dlie"], flags=c["st2"]["flags"])
+        s.set_friction(np.array([prob.fault.f + sgn * h]))
+        s.step(prob.dts[2], newton_rtol=1e-12)
+        st = s.get_state()
+        Js.append(J_of(st["slip"].T, st["p"], c["obs_pairs"], c["obs_nodes"]))
+    s.set_friction(np.array([prob.fault.f]))
+    fd = (Js[0] - Js[1]) / (2 * h)
+    assert c["gf"].sum() == pytest.approx(fd, rel=1e-5)
+
+
+def test_autograd_function_gradients():
+    need_gpu()
+    import paper_2410_17133_gb300 as gm
+    prob, obs_pairs, obs_nodes = scenario()
+    s = solver_for(prob)
+    for dt in prob.dts[:2]:
+        s.step(dt, newton_rtol=1e-12)
+    Fn = gm.implicit_step_fn()
+    logk = torch.tensor(np.log(np.asarray(prob.k, float)), device="cuda", requires_grad=True)
+    f = torch.tensor(prob.fault.f, dtype=torch.float64, device="cuda", requires_grad=True)
+    logQ = torch.tensor(0.0, dtype=torch.float64, device="cuda", requires_grad=True)
+    slip, p = Fn.apply(logk, f, logQ, s, prob.dts[2], (prob.fu, prob.fp), {"newton_rtol": 1e-12})
+    op = torch.as_tensor(obs_pairs, device="cuda")
+    on = torch.as_tensor(obs_nodes, device="cuda")
+    J = (slip[:, op] ** 2).sum() / S0 ** 2 + p[on].sum() / P0
+    J.backward()
+    st3 = s.get_state()
+    g_s, g_p = dJ(st3["slip"].T, obs_pairs, obs_nodes, s.N)
+    gk, gf, gq, _ = s.adjoint(dJ_dp=cuda(g_p), dJ_dslip=cuda(g_s.T), rtol=1e-11)
+    assert rel(logk.grad.cpu().numpy(), gk.cpu().numpy()) < 1e-8
+    assert f.grad.item() == pytest.approx(gf.sum().item(), rel=1e-8)
+    assert logQ.grad.item() == pytest.approx(gq, rel=1e-8)
