@@ -226,6 +226,7 @@ inline void gm_bulk_geometry(const gm_ctx* c, int* gx, int* gy, int* gz, int* zc
     if (nzc < 1) nzc = 1;
     int zc = (c->g.nplanes + nzc - 1) / nzc;
     if (zc < 4) zc = 4;
+    if (c->zchunk_override > 0) zc = c->zchunk_override;
     *zchunk = zc;
     *gz = (c->g.nplanes + zc - 1) / zc;
 }

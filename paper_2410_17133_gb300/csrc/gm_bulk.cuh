@@ -140,10 +140,14 @@ gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
 
     // xy part of the forward transform for this thread's face:
     // t[sx + 2 sy] = sum_{ax,ay} (-1)^(sx ax + sy ay) v[ax, ay]
+    // own_next: this thread's own node (tile node (tx, ty)) of the plane last
+    // transformed; in PCG mode it is the node's new direction value p
+    T own_next[NI];
     auto fwd_xy = [&](int buf, T (&t)[NI][4]) {
 #pragma unroll
         for (int f = 0; f < NI; ++f) {
             const T v00 = s_plane[buf][f][ty * 17 + tx], v10 = s_plane[buf][f][ty * 17 + tx + 1];
+            own_next[f] = v00;
             const T v01 = s_plane[buf][f][(ty + 1) * 17 + tx], v11 = s_plane[buf][f][(ty + 1) * 17 + tx + 1];
             const T a0 = v00 + v10, a1 = v00 - v10, b0 = v01 + v11, b1 = v01 - v11;
             t[f][0] = a0 + b0;
@@ -273,6 +277,9 @@ gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
     store(buf);
 
     double dot = 0.0;
+    T own_cur[NI];
+#pragma unroll
+    for (int f = 0; f < NI; ++f) own_cur[f] = own_next[f];   // plane z0
     for (int kk = z0; kk < z1; ++kk) {
         // buffer `buf` holds plane kk + 1 (if it exists); fetch plane kk + 2
         const bool need_next = kk + 2 < g.nplanes && kk + 2 <= z1;
@@ -310,6 +317,8 @@ gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
         }
         if (need_next) store(buf ^ 1);
         __syncthreads();
+        // own values of plane kk (for its node stage below) were stashed when plane kk
+        // was transformed; own_next now holds plane kk + 1 (transformed this iteration)
         // node stage: node (tx, ty) of the tile sums its four faces
         if (tx >= 1 && ty >= 1) {
             const int gi = x0 - 1 + tx, gj = y0 - 1 + ty;
@@ -317,6 +326,7 @@ gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
                 const long long node = gi + rowlen * (gj + (long long)(g.ny + 1) * kk);
                 const unsigned m = a.mask[node];
                 const bool lip = g.kf >= 0 && (kk == g.kf || kk == g.kf + 1);
+                T ndot = T(0);
 #pragma unroll
                 for (int f = 0; f < NO; ++f) {
                     const T v = s_face[f][0][tid] + s_face[f][1][tid - 1] +
@@ -325,9 +335,9 @@ gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
                         const T y = ((m >> f) & 1u) ? T(0) : v;
                         a.yu[f * N + node] = y;
                         if constexpr (PCG) {
-                            const T pn = ((m >> f) & 1u) ? T(0) : in_u(f, node);
-                            a.pu_new[f * N + node] = pn;
-                            if (!lip) dot += (double)pn * (double)y;
+                            // own_cur holds z + beta p_old of this node, masked at load
+                            a.pu_new[f * N + node] = own_cur[f];
+                            if (!lip) ndot = fma(own_cur[f], y, ndot);
                         }
                     } else {
                         // raw value on a tied slave lip: the fault kernel folds it
@@ -335,15 +345,20 @@ gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
                         const T y = (!slave && ((m >> 3) & 1u)) ? T(0) : v;
                         a.yp[node] = y;
                         if constexpr (PCG) {
-                            const T pn = (slave || ((m >> 3) & 1u)) ? T(0) : in_p(node);
+                            const T pn = slave ? T(0) : own_cur[IPI];
                             a.pp_new[node] = pn;
+                            // pressure-system products in FP64 (FP32 squares of flow
+                            // quantities can underflow)
                             if (!lip) dot += (double)pn * (double)y;
                         }
                     }
                 }
+                dot += (double)ndot;
             }
         }
         buf ^= 1;
+#pragma unroll
+        for (int f = 0; f < NI; ++f) own_cur[f] = own_next[f];
     }
 
     if constexpr (PCG) {

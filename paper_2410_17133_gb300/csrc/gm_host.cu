@@ -1,6 +1,7 @@
 // Context, set-up, reference-cell operators, Newton driver and the C ABI.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "gm_internal.cuh"
@@ -815,12 +816,15 @@ int bind_impl(gm_ctx* c)
     // device allocation
     const long long P = c->P;
     const long long N3 = 3 * N;
+    // optional tuning override of the bulk kernel's plane-chunk length
+    if (const char* zc = std::getenv("GM_BULK_ZCHUNK")) c->zchunk_override = std::max(0, std::atoi(zc));
     // reduction partials: the fixed-grid reductions use 2 * GM_RED_BLOCKS slots,
     // a fused PCG step one per bulk CTA plus one per fault block
     const int gxp = (c->nx + 1 + 14) / 15, gyp = (c->ny + 1 + 14) / 15;
     const long long xyp = (long long)gxp * gyp;
     const long long nzc = std::max(1LL, (4LL * c->sm_count + xyp - 1) / xyp);
-    const long long zcp = std::max(4LL, (c->g.nplanes + nzc - 1) / nzc);
+    const long long zcp = c->zchunk_override > 0 ? (long long)c->zchunk_override
+                                                 : std::max(4LL, (c->g.nplanes + nzc - 1) / nzc);
     c->bulk_grid = (int)(xyp * ((c->g.nplanes + zcp - 1) / zcp));
     const size_t part_bytes = (size_t)8 * std::max<long long>(4LL * GM_RED_BLOCKS,
                                                               c->bulk_grid + (c->g.nb + 255) / 256 + 64);

@@ -272,6 +272,7 @@ struct gm_ctx {
     DevBuf k_r32, k_z32, k_p32, k_pb32, k_q32, k_x32, k_b32;      // inner PCG (FP32)
     DevBuf a_r32, a_z32, a_p32, a_pb32, a_q32, a_x32, a_b32;
     int bulk_grid = 0;                                 // CTAs of one bulk apply
+    int zchunk_override = 0;                           // GM_BULK_ZCHUNK (tuning), 0 = heuristic
     DevBuf o_y1, o_w, o_x1, o_t3, o_r, o_z, o_zold, o_p, o_q, o_x2, o_t1;   // outer CG
     DevBuf dprevstate;
     void* hpin = nullptr;                              // pinned host scratch (4 KB)

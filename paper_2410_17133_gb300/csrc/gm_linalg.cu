@@ -90,6 +90,32 @@ struct Prec<T, 1> {
     }
 };
 
+// Add r.z and r.r of one node to the FP64 accumulators v.  Displacement
+// vectors (3 components, force-scale residuals) sum the node's components in
+// the vector precision first; pressure vectors (flow residuals of order
+// 1e-15..1e-20 m^3, whose squares would underflow in FP32) multiply in FP64,
+// where the product of two floats is exact.
+template <typename T, int NC>
+__device__ inline void gm_dot_node(const T (&r)[NC], const T (&z)[NC], double (&v)[2])
+{
+    if constexpr (NC == 3) {
+        T a = T(0), b = T(0);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            a = fma(r[c], z[c], a);
+            b = fma(r[c], r[c], b);
+        }
+        v[0] += (double)a;
+        v[1] += (double)b;
+    } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            v[0] += (double)r[c] * (double)z[c];
+            v[1] += (double)r[c] * (double)r[c];
+        }
+    }
+}
+
 struct RedCtx {
     double* part;
     unsigned* counter;
@@ -113,10 +139,8 @@ gm_pcg_init_kernel(long long N, const T* b, const T* q, T* r, T* z, T* p, const 
             r[c * N + n] = rr[c];
             z[c * N + n] = zz[c];
             p[c * N + n] = T(0);   // previous direction: the first step is p = z
-            // products of T values are exact in double; the sums accumulate in FP64
-            v[0] += (double)rr[c] * (double)zz[c];
-            v[1] += (double)rr[c] * (double)rr[c];
         }
+        gm_dot_node<T, NC>(rr, zz, v);
     }
     if (gm_grid_sum_l<2>(v, rc.part, rc.counter)) {
         sc->rz = v[0];
@@ -152,11 +176,8 @@ gm_pcg_update_kernel(long long N, T* x, T* r, T* z, const T* p, const T* q, cons
         }
         Prec<T, WHICH>::apply(mi, N, n, rr, zz);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            z[c * N + n] = zz[c];
-            v[0] += (double)rr[c] * (double)zz[c];
-            v[1] += (double)rr[c] * (double)rr[c];
-        }
+        for (int c = 0; c < NC; ++c) z[c * N + n] = zz[c];
+        gm_dot_node<T, NC>(rr, zz, v);
     }
     if (gm_grid_sum_l<2>(v, rc.part, rc.counter)) {
         sc->it += 1;
