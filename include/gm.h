@@ -254,6 +254,25 @@ int gm_adjoint_step(gm_ctx* ctx, const double* dJ_du_dev, const double* dJ_dp_de
                     double* g_logQ_host, double rtol, int maxit, gm_solve_report* report_host,
                     void* stream);
 
+/* One step of the reverse sweep of a multi-step adjoint, for objectives of
+ * the state after several implicit steps, with the inelastic slip carried
+ * from step to step as history (Eq. plastic_slip_increment).  The context must
+ * hold this step's state: accepted u_n, p_n and the inelastic slip h_{n-1}
+ * before the step (gm_set_state), its dt (gm_set_timestep), and the return
+ * map at u_n (gm_fault_update).  Inputs from the later step n+1 (all NULL at
+ * the last step): lam_next_dev (4N) its adjoint, mu_next_dev (2 per pair) its
+ * history adjoint, frozen_next_dev (6 per pair) its frozen pair data.  Direct
+ * objective terms dJ_* as in gm_adjoint_step (usually only at the last step).
+ * Outputs: lam_dev (4N), mu_dev (2 per pair), frozen_dev (6 per pair) for the
+ * earlier step, and this step's gradient contributions g_logk_dev, g_f_dev,
+ * g_logQ_host (overwritten; the caller sums over steps).  Synchronises. */
+int gm_adjoint_sweep_step(gm_ctx* ctx, const double* dJ_du_dev, const double* dJ_dp_dev,
+                          const double* dJ_dslip_dev, const double* lam_next_dev,
+                          const double* mu_next_dev, const double* frozen_next_dev,
+                          double* lam_dev, double* mu_dev, double* frozen_dev,
+                          double* g_logk_dev, double* g_f_dev, double* g_logQ_host,
+                          double rtol, int maxit, gm_solve_report* report_host, void* stream);
+
 /* ---- state I/O (checkpoint / resume) --------------------------------- */
 
 /* Copy the accepted state to host arrays (any may be NULL): u (3N), p (N, tied

@@ -89,6 +89,8 @@ _SIG = {
     "gm_set_friction": (C.c_int, [_P, _D, C.c_int64]),
     "gm_adjoint_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _D, C.c_double, C.c_int,
                                   C.POINTER(SolveReport), _P]),
+    "gm_adjoint_sweep_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _D,
+                                        C.c_double, C.c_int, C.POINTER(SolveReport), _P]),
 }
 
 _lib = None
@@ -348,6 +350,28 @@ class Solver:
                                           C.byref(gq), rtol, maxit, C.byref(rep), _stream_ptr(stream)))
         return gk, gf[:self.P], gq.value, dict(iterations=rep.iterations, rel_residual=rep.rel_residual)
 
+    def adjoint_sweep_step(self, dJ_du=None, dJ_dp=None, dJ_dslip=None, lam_next=None,
+                           mu_next=None, frozen_next=None, rtol=1e-10, maxit=300, stream=None):
+        """gm_adjoint_sweep_step: one step of a multi-step reverse sweep (the
+        context must hold the step's state and return map).  Returns
+        (lam (4, N), mu (2, P), frozen (6, P), g_logk, g_f, g_logQ)."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        f64 = dict(dtype=torch.float64, device=dev)
+        lam = torch.empty((4, self.N), **f64)
+        mu = torch.empty((2, self.P), **f64)
+        fz = torch.empty((6, self.P), **f64)
+        gk = torch.empty(self.n_el, **f64)
+        gf = torch.empty(self.P, **f64)
+        gq = C.c_double()
+        rep = SolveReport()
+        ins = [None if t is None else t.contiguous() for t in (dJ_du, dJ_dp, dJ_dslip, lam_next, mu_next, frozen_next)]
+        ptr = [None if t is None else _tptr(t) for t in ins]
+        self._chk(self._L.gm_adjoint_sweep_step(self.h, *ptr, _tptr(lam), _tptr(mu), _tptr(fz), _tptr(gk),
+                                                _tptr(gf), C.byref(gq), rtol, maxit, C.byref(rep),
+                                                _stream_ptr(stream)))
+        return lam, mu, fz, gk, gf, gq.value
+
     def counters(self):
         """(kernel launches, bulk operator applies) since bind."""
         a, b = C.c_int64(), C.c_int64()
@@ -392,3 +416,53 @@ def implicit_step_fn():
                     None, None, None, None)
 
     return ImplicitStep
+
+
+def run_with_adjoint(solver, dts, objective_grad, checkpoint_every=5, step_kw=None, rtol=1e-10):
+    """Run len(dts) implicit steps from the solver's current state, then the
+    reverse sweep of the multi-step adjoint (inelastic slip as history).
+
+    objective_grad(final_state) returns (dJ_du, dJ_dp, dJ_dslip) for an
+    objective of the final state (CUDA float64 tensors shaped (3, N), (N,),
+    (2, P), or None).  Forward states are checkpointed on the host every
+    `checkpoint_every` steps; each segment is recomputed from its checkpoint
+    during the sweep.  Every computation runs in the library; this function
+    only sequences calls.  Returns (final_state, g_logk, g_f, g_logQ) with
+    g_f per pair; the solver ends holding the final state."""
+    import torch
+    kw = dict(step_kw or {})
+    K = len(dts)
+    dev = torch.device("cuda", solver.device)
+    ckpt = {0: solver.get_state()}
+    for n in range(K):
+        solver.step(dts[n], **kw)
+        if (n + 1) % checkpoint_every == 0 and n + 1 < K:
+            ckpt[n + 1] = solver.get_state()
+    final = solver.get_state()
+    dJ_du, dJ_dp, dJ_dslip = objective_grad(final)
+    g_logk = torch.zeros(solver.n_el, dtype=torch.float64, device=dev)
+    g_f = torch.zeros(solver.P, dtype=torch.float64, device=dev)
+    g_logQ = 0.0
+    lam = mu = fz = None
+    starts = sorted(ckpt)
+    for si, s0 in enumerate(reversed(starts)):
+        s1 = K if si == 0 else starts[len(starts) - si]
+        solver.set_state(u=ckpt[s0]["u"], p=ckpt[s0]["p"], dlie=ckpt[s0]["dlie"], flags=ckpt[s0]["flags"])
+        states = {s0: ckpt[s0]}
+        for n in range(s0, s1):
+            solver.step(dts[n], **kw)
+            states[n + 1] = solver.get_state()
+        for n in range(s1, s0, -1):
+            st, prev = states[n], states[n - 1]
+            solver.set_state(u=st["u"], p=st["p"], dlie=prev["dlie"], flags=st["flags"])
+            solver.timestep(dts[n - 1])
+            solver.fault_update(torch.as_tensor(st["u"], device=dev))
+            last = n == K
+            lam, mu, fz, gk, gf, gq = solver.adjoint_sweep_step(
+                dJ_du if last else None, dJ_dp if last else None, dJ_dslip if last else None,
+                lam, mu, fz, rtol=rtol)
+            g_logk += gk
+            g_f += gf
+            g_logQ += gq
+    solver.set_state(u=final["u"], p=final["p"], dlie=final["dlie"], flags=final["flags"])
+    return final, g_logk, g_f, g_logQ

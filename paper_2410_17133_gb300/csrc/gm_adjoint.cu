@@ -112,6 +112,95 @@ __global__ void adj_grad_f_kernel(GridDesc g, const double* lu, const double* tn
     gf[i] = -Ai * tn[i] * d;
 }
 
+// Frozen pair data of the current return map, 6 per pair (field-major):
+// state, t'_n, |t^tr|, F, tau_1, tau_2 (slip direction in the fault frame).
+__global__ void adj_frozen_kernel(long long P, const int8_t* st, const double* tn, const double* F,
+                                  const double* tauc, const double* fpair, double fs, double t1x,
+                                  double t1y, double t1z, double t2x, double t2y, double t2z, double* out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const double f = fpair ? fpair[i] : fs;
+    const double tx = tauc[i], ty = tauc[P + i], tz = tauc[2 * P + i];
+    out[i] = (double)st[i];
+    out[P + i] = tn[i];
+    out[2 * P + i] = F[i] + f * tn[i];                // |t^tr|
+    out[3 * P + i] = F[i];
+    out[4 * P + i] = tx * t1x + ty * t1y + tz * t1z;
+    out[5 * P + i] = tx * t2x + ty * t2y + tz * t2z;
+}
+
+// mu_n = -(dF_{n+1}/dh_n)^T lambda_{n+1} + (dH_{n+1}/dh_n)^T mu_{n+1}, with the
+// later step's frozen data fz (see the multi-step reverse sweep).
+__global__ void adj_mu_kernel(GridDesc g, const double* fz, const double* lam_u, const double* mu_next,
+                              const double* fpair, double fs, double ks, double Aq, double t1x, double t1y,
+                              double t1z, double t2x, double t2y, double t2z, double* mu)
+{
+    const long long P = g.nb;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const long long N = g.N;
+    const long long nm = i + g.nb * g.kf, np = nm + g.nb;
+    const int pi = (int)(i % (g.nx + 1)), pj = (int)(i / (g.nx + 1));
+    const int nqi = (pi > 0) + (pi < g.nx), nqj = (pj > 0) + (pj < g.ny);
+    const double Ai = Aq * 0.25 * nqi * nqj;
+    const double dx = lam_u[np] - lam_u[nm], dy = lam_u[N + np] - lam_u[N + nm];
+    const double dz = lam_u[2 * N + np] - lam_u[2 * N + nm];
+    const double d1 = dx * t1x + dy * t1y + dz * t1z, d2 = dx * t2x + dy * t2y + dz * t2z;
+    const int st = (int)fz[i];
+    const double m1 = mu_next ? mu_next[i] : 0.0, m2 = mu_next ? mu_next[P + i] : 0.0;
+    double o1 = 0.0, o2 = 0.0;
+    if (st == GM_STICK) {
+        o1 = Ai * ks * d1 + m1;
+        o2 = Ai * ks * d2 + m2;
+    } else if (st == GM_SLIP) {
+        const double f = fpair ? fpair[i] : fs;
+        const double tn = fz[P + i], nt = fz[2 * P + i], F = fz[3 * P + i];
+        const double a = fz[4 * P + i], b = fz[5 * P + i];
+        const double r = f * tn / nt;
+        const double dp = a * d1 + b * d2, mp = a * m1 + b * m2;
+        const double c1 = 1.0 - F / nt;
+        o1 = Ai * ks * r * (d1 - a * dp) + c1 * (m1 - a * mp);
+        o2 = Ai * ks * r * (d2 - b * dp) + c1 * (m2 - b * mp);
+    } else {
+        o1 = m1;
+        o2 = m2;
+    }
+    mu[i] = o1;
+    mu[P + i] = o2;
+}
+
+// (dH_n/dx_n)^T mu_n added on the lips of b (this step's frozen data fz), and
+// mu^T dH/df into gf (added).
+__global__ void adj_hist_rhs_kernel(GridDesc g, const double* fz, const double* mu, const double* fpair,
+                                    double fs, double kn, double ks, double t1x, double t1y, double t1z,
+                                    double t2x, double t2y, double t2z, double nx_, double ny_, double nz_,
+                                    const uint8_t* mask, double* b, double* gf)
+{
+    const long long P = g.nb;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    if ((int)fz[i] != GM_SLIP) return;
+    const long long N = g.N;
+    const long long nm = i + g.nb * g.kf, np = nm + g.nb;
+    const double f = fpair ? fpair[i] : fs;
+    const double tn = fz[P + i], nt = fz[2 * P + i], F = fz[3 * P + i];
+    const double a = fz[4 * P + i], bb = fz[5 * P + i];
+    const double m1 = mu[i], m2 = mu[P + i];
+    const double tm = a * m1 + bb * m2;
+    const double ratio = F / nt;
+    const double g1 = a * tm + ratio * (m1 - a * tm), g2 = bb * tm + ratio * (m2 - bb * tm);
+    const double gn = f * kn / ks * tm;
+    const double v[3] = {g1 * t1x + g2 * t2x + gn * nx_, g1 * t1y + g2 * t2y + gn * ny_,
+                         g1 * t1z + g2 * t2z + gn * nz_};
+    const unsigned mp = mask[np], mm = mask[nm];
+    for (int c = 0; c < 3; ++c) {
+        if (!((mp >> c) & 1u)) b[c * N + np] += v[c];
+        if (!((mm >> c) & 1u)) b[c * N + nm] -= v[c];
+    }
+    if (gf) gf[i] += -(tn / ks) * tm;
+}
+
 int ensure_adjoint_buffers(gm_ctx* c, int m)
 {
     if (c->adj_m >= m) return GM_OK;
@@ -200,27 +289,17 @@ extern "C" int gm_set_friction(gm_ctx* c, const double* f, int64_t n)
     return GM_OK;
 }
 
-extern "C" int gm_adjoint_step(gm_ctx* c, const double* dJ_du, const double* dJ_dp, const double* dJ_dslip,
-                               double* g_logk, double* g_f, double* g_logQ, double rtol, int maxit,
-                               gm_solve_report* rep, void* stream)
+// FGMRES solve of J_cons^T x = b (b in adj_b, x in adj_x).
+static int adj_solve(gm_ctx* c, double rtol, int maxit, gm_solve_report* rep, cudaStream_t s)
 {
-    if (!c) return GM_EINVAL;
-    if (!c->bound) return c->set_err(GM_ESTATE, "adjoint: not bound");
-    if (!(rtol > 0) || maxit < 1) return c->set_err(GM_EINVAL, "adjoint: bad tolerance or maxit");
-    cudaStream_t s = (cudaStream_t)stream;
     const long long N = c->N, n4 = 4 * N;
     const int m = 30;
-    int rc = ensure_adjoint_buffers(c, m);
-    if (rc) return rc;
     double* V = c->adj_V.as<double>();
     double* Z = c->adj_Z.as<double>();
     double* w = c->adj_w.as<double>();
     double* b = c->adj_b.as<double>();
     double* x = c->adj_x.as<double>();
-    const int nb = (int)((N + 255) / 256);
-    adj_rhs_kernel<<<nb, 256, 0, s>>>(c->g, dJ_du, dJ_dp, dJ_dslip, c->dmask.as<uint8_t>(), c->t1[0],
-                                      c->t1[1], c->t1[2], c->t2[0], c->t2[1], c->t2[2], b);
-    GM_LAUNCHED(c);
+    int rc;
     if ((rc = gm_launch_block_jacobi(c, s))) return rc;   // symmetric Newton tangent of the frozen state
     GM_CUDA_TRY(c, cudaMemsetAsync(x, 0, n4 * sizeof(double), s));
     double beta0;
@@ -300,8 +379,18 @@ extern "C" int gm_adjoint_step(gm_ctx* c, const double* dJ_du, const double* dJ_
         rep->rel_residual = beta0 > 0 ? rfin / beta0 : 0.0;
         rep->status = GM_OK;
     }
-    const double* lu = x;
-    const double* lp = x + 3 * N;
+    if (beta0 > 0 && rfin > 10 * rtol * beta0)
+        return c->set_err(GM_ENOCONV, "adjoint: GMRES did not reach the tolerance (" + std::to_string(rfin / beta0) + ")");
+    return GM_OK;
+}
+
+// gradients of this step from lambda (adj_x): -lambda^T dF/dtheta
+static int adj_gradients(gm_ctx* c, double* g_logk, double* g_f, double* g_logQ, cudaStream_t s)
+{
+    const long long N = c->N;
+    const double* lu = c->adj_x.as<double>();
+    const double* lp = lu + 3 * N;
+    int rc;
     if (g_logk) {
         GradArgs ga;
         ga.g = c->g;
@@ -324,8 +413,98 @@ extern "C" int gm_adjoint_step(gm_ctx* c, const double* dJ_du, const double* dJ_
         if ((rc = dot(c, N, lp, c->dfp.as<double>(), &d, s))) return rc;
         *g_logQ = c->dt * d;
     }
-    GM_CUDA_TRY(c, cudaStreamSynchronize(s));
-    if (beta0 > 0 && rfin > 10 * rtol * beta0)
-        return c->set_err(GM_ENOCONV, "adjoint: GMRES did not reach the tolerance (" + std::to_string(rfin / beta0) + ")");
     return GM_OK;
+}
+
+static int adj_rhs(gm_ctx* c, const double* dJ_du, const double* dJ_dp, const double* dJ_dslip,
+                   cudaStream_t s)
+{
+    const int nb = (int)((c->N + 255) / 256);
+    adj_rhs_kernel<<<nb, 256, 0, s>>>(c->g, dJ_du, dJ_dp, dJ_dslip, c->dmask.as<uint8_t>(), c->t1[0],
+                                      c->t1[1], c->t1[2], c->t2[0], c->t2[1], c->t2[2], c->adj_b.as<double>());
+    GM_LAUNCHED(c);
+    return GM_OK;
+}
+
+extern "C" int gm_adjoint_step(gm_ctx* c, const double* dJ_du, const double* dJ_dp, const double* dJ_dslip,
+                               double* g_logk, double* g_f, double* g_logQ, double rtol, int maxit,
+                               gm_solve_report* rep, void* stream)
+{
+    if (!c) return GM_EINVAL;
+    if (!c->bound) return c->set_err(GM_ESTATE, "adjoint: not bound");
+    if (!(rtol > 0) || maxit < 1) return c->set_err(GM_EINVAL, "adjoint: bad tolerance or maxit");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ensure_adjoint_buffers(c, 30);
+    if (rc) return rc;
+    if ((rc = adj_rhs(c, dJ_du, dJ_dp, dJ_dslip, s))) return rc;
+    const int rs = adj_solve(c, rtol, maxit, rep, s);
+    if (rs && rs != GM_ENOCONV) return rs;
+    if ((rc = adj_gradients(c, g_logk, g_f, g_logQ, s))) return rc;
+    GM_CUDA_TRY(c, cudaStreamSynchronize(s));
+    return rs;
+}
+
+extern "C" int gm_adjoint_sweep_step(gm_ctx* c, const double* dJ_du, const double* dJ_dp,
+                                     const double* dJ_dslip, const double* lam_next, const double* mu_next,
+                                     const double* frozen_next, double* lam, double* mu, double* frozen,
+                                     double* g_logk, double* g_f, double* g_logQ, double rtol, int maxit,
+                                     gm_solve_report* rep, void* stream)
+{
+    if (!c) return GM_EINVAL;
+    if (!c->bound || !c->has_fault) return c->set_err(GM_ESTATE, "adjoint sweep: needs a bound fault");
+    if (!lam || !mu || !frozen) return c->set_err(GM_EINVAL, "adjoint sweep: null output");
+    if ((lam_next == nullptr) != (frozen_next == nullptr))
+        return c->set_err(GM_EINVAL, "adjoint sweep: lam_next and frozen_next go together");
+    if (!(rtol > 0) || maxit < 1) return c->set_err(GM_EINVAL, "adjoint: bad tolerance or maxit");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ensure_adjoint_buffers(c, 30);
+    if (rc) return rc;
+    const long long N = c->N, P = c->P;
+    const int pb = (int)((P + 255) / 256);
+    const double* fpair = c->has_fpair ? c->dfpair.as<double>() : nullptr;
+    // this step's frozen pair data
+    adj_frozen_kernel<<<pb, 256, 0, s>>>(P, c->dstate.as<int8_t>(), c->dtn.as<double>(), c->dF.as<double>(),
+                                         c->dtauc.as<double>(), fpair, c->fp.f, c->t1[0], c->t1[1], c->t1[2],
+                                         c->t2[0], c->t2[1], c->t2[2], frozen);
+    GM_LAUNCHED(c);
+    // mu_n from the later step
+    if (lam_next) {
+        adj_mu_kernel<<<pb, 256, 0, s>>>(c->g, frozen_next, lam_next, mu_next, fpair, c->fp.f, c->fp.ks, c->Aq,
+                                         c->t1[0], c->t1[1], c->t1[2], c->t2[0], c->t2[1], c->t2[2], mu);
+        GM_LAUNCHED(c);
+    } else if (mu_next) {
+        GM_CUDA_TRY(c, cudaMemcpyAsync(mu, mu_next, 2 * P * 8, cudaMemcpyDeviceToDevice, s));
+    } else {
+        GM_CUDA_TRY(c, cudaMemsetAsync(mu, 0, 2 * P * 8, s));
+    }
+    // right-hand side: direct terms + [A_pu l_p ; S l_p]_{n+1} + (dH_n/dx_n)^T mu_n
+    if ((rc = adj_rhs(c, dJ_du, dJ_dp, dJ_dslip, s))) return rc;
+    double* b = c->adj_b.as<double>();
+    double* t = c->adj_t.as<double>();
+    if (lam_next) {
+        if ((rc = gm_launch_apply_f64(c, GM_MODE_APU, 0, 1, 0, 0, 0, nullptr, lam_next + 3 * N, t, nullptr, s, nullptr))) return rc;
+        if ((rc = gm_launch_axpby(c, 3 * N, 1.0, t, 1.0, b, s))) return rc;
+        if ((rc = gm_launch_apply_f64(c, GM_MODE_A22, 0, 0, 0, 1, 0, nullptr, lam_next + 3 * N, nullptr, t + 3 * N, s, nullptr))) return rc;
+        if ((rc = gm_launch_axpby(c, N, 1.0, t + 3 * N, 1.0, b + 3 * N, s))) return rc;
+    }
+    if (g_f) GM_CUDA_TRY(c, cudaMemsetAsync(g_f, 0, P * 8, s));
+    double* hist_gf = c->adj_w.as<double>();      // mu^T dH/df, reused below
+    GM_CUDA_TRY(c, cudaMemsetAsync(hist_gf, 0, P * 8, s));
+    adj_hist_rhs_kernel<<<pb, 256, 0, s>>>(c->g, frozen, mu, fpair, c->fp.f, c->fp.kn, c->fp.ks, c->t1[0], c->t1[1],
+                                           c->t1[2], c->t2[0], c->t2[1], c->t2[2], c->nrm[0], c->nrm[1], c->nrm[2],
+                                           c->dmask.as<uint8_t>(), b, hist_gf);
+    GM_LAUNCHED(c);
+    std::vector<double> hgf(P);
+    GM_CUDA_TRY(c, cudaMemcpyAsync(hgf.data(), hist_gf, P * 8, cudaMemcpyDeviceToHost, s));
+    GM_CUDA_TRY(c, cudaStreamSynchronize(s));
+    const int rs = adj_solve(c, rtol, maxit, rep, s);
+    if (rs && rs != GM_ENOCONV) return rs;
+    if ((rc = adj_gradients(c, g_logk, g_f, g_logQ, s))) return rc;
+    if (g_f) {
+        GM_CUDA_TRY(c, cudaMemcpyAsync(hist_gf, hgf.data(), P * 8, cudaMemcpyHostToDevice, s));
+        if ((rc = gm_launch_axpby(c, P, 1.0, hist_gf, 1.0, g_f, s))) return rc;
+    }
+    GM_CUDA_TRY(c, cudaMemcpyAsync(lam, c->adj_x.p, 4 * N * 8, cudaMemcpyDeviceToDevice, s));
+    GM_CUDA_TRY(c, cudaStreamSynchronize(s));
+    return rs;
 }

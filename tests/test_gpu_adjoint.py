@@ -131,3 +131,62 @@ def test_autograd_function_gradients():
     assert rel(logk.grad.cpu().numpy(), gk.cpu().numpy()) < 1e-8
     assert f.grad.item() == pytest.approx(gf.sum().item(), rel=1e-8)
     assert logQ.grad.item() == pytest.approx(gq, rel=1e-8)
+
+
+def test_multistep_adjoint_matches_oracle_and_fd():
+    """Four steps with slipping pairs, checkpoints every 2 steps: gradients of an
+    objective of the final state equal the oracle's multi-step adjoint, and a
+    random-direction derivative equals central finite differences of GPU runs."""
+    need_gpu()
+    import paper_2410_17133_gb300 as gm
+    from oracle import adjoint as oadj
+    prob = W.fault_small(n=6, Q=5e-5, steps=4)
+    K = 4
+    rng = np.random.default_rng(9)
+    obs_pairs = rng.choice(prob.n_pairs, 12, replace=False)
+    obs_nodes = rng.choice(prob.n_nodes, 8, replace=False)
+    kw = {"newton_rtol": 1e-12}
+
+    def objective_grad(st):
+        g_s, g_p = dJ(st["slip"].T, obs_pairs, obs_nodes, prob.n_nodes)
+        return None, cuda(g_p), cuda(g_s.T)
+
+    s = solver_for(prob)
+    final, gk, gf, gq = gm.run_with_adjoint(s, prob.dts[:K], objective_grad, checkpoint_every=2,
+                                            step_kw=kw, rtol=1e-11)
+    assert (final["flags"] == 2).sum() >= 5
+    # oracle
+    model = fem.Model(prob)
+    st = osolve.initial_state(model)
+    traj = []
+    for dt in prob.dts[:K]:
+        h_prev = st.dlie.copy()
+        osolve.implicit_step(model, st, dt, rtol=1e-13)
+        traj.append(dict(u=st.u.copy(), p=st.p.copy(), h_prev=h_prev))
+    res_slip = model.jump(st.u)
+    g_s_o = np.zeros((prob.n_pairs, 2))
+    gsl = np.stack([np.sum(model.fg["t1"] * res_slip, 1), np.sum(model.fg["t2"] * res_slip, 1)], 1)
+    g_s_o[obs_pairs] = 2 * gsl[obs_pairs] / S0 ** 2
+    g_p_o = np.zeros(model.N)
+    np.add.at(g_p_o, obs_nodes, 1.0 / P0)
+    go = oadj.adjoint_multistep(model, traj, prob.dts[:K], dJ_dp=g_p_o, dJ_dslip=g_s_o)
+    assert rel(gk.cpu().numpy(), go["g_logk"]) < 1e-6
+    assert rel(gf.cpu().numpy(), go["g_f"]) < 1e-6
+    assert gq == pytest.approx(go["g_logQ"], rel=1e-6)
+    # finite differences on the GPU along one random direction
+    k0 = np.asarray(prob.k, float)
+    vk, vf, vq = rng.normal(size=k0.size), rng.normal(), rng.normal()
+    pred = gk.cpu().numpy() @ vk + gf.sum().item() * vf + gq * vq
+    h = 1e-5
+    Js = []
+    for sgn in (1, -1):
+        s2 = solver_for(prob)
+        s2.set_permeability(k0 * np.exp(sgn * h * vk))
+        s2.set_friction(np.array([prob.fault.f + sgn * h * vf]))
+        s2.loads(prob.fu, prob.fp * math.exp(sgn * h * vq))
+        for dt in prob.dts[:K]:
+            s2.step(dt, newton_rtol=1e-12)
+        stt = s2.get_state()
+        Js.append(J_of(stt["slip"].T, stt["p"], obs_pairs, obs_nodes))
+    fd = (Js[0] - Js[1]) / (2 * h)
+    assert pred == pytest.approx(fd, rel=1e-5)

@@ -108,3 +108,56 @@ def test_gradient_element_permeability(case):
             J.append(objective(r, case["obs_pairs"], case["obs_nodes"]))
         fd = (J[0] - J[1]) / (2 * h)
         assert g[e] == pytest.approx(fd, rel=1e-5, abs=1e-9 * np.abs(g).max())
+
+
+# ---------------------------------------------------------------------------
+# several steps (inelastic slip carried as history), random directions
+# ---------------------------------------------------------------------------
+
+def run_traj(prob, steps, k=None, f=None, qscale=1.0):
+    p2 = copy.deepcopy(prob)
+    if k is not None:
+        p2.k = k
+    model = fem.Model(p2)
+    model.fpv = model.fpv * qscale
+    st = solve.initial_state(model)
+    traj = []
+    for dt in prob.dts[:steps]:
+        h_prev = st.dlie.copy()
+        r = solve.implicit_step(model, st, dt, rtol=1e-13, f=f)
+        pm = st.p.copy()
+        traj.append(dict(u=st.u.copy(), p=pm, h_prev=h_prev, res=r))
+    return model, traj
+
+
+def test_multistep_adjoint_directional_derivatives():
+    prob = W.fault_small(n=6, Q=5e-5, steps=4)
+    K = 4
+    model, traj = run_traj(prob, K)
+    final = traj[-1]["res"]
+    assert (final.flags == 2).sum() >= 5
+    rng = np.random.default_rng(9)
+    P = final.slip.shape[0]
+    obs_pairs = rng.choice(P, 12, replace=False)
+    obs_nodes = rng.choice(model.N, 8, replace=False)
+    dJ_dslip = np.zeros((P, 2))
+    dJ_dslip[obs_pairs] = 2 * final.slip[obs_pairs] / S0 ** 2
+    dJ_dp = np.zeros(model.N)
+    np.add.at(dJ_dp, obs_nodes, 1.0 / P0)
+    g = adjoint.adjoint_multistep(model, traj, prob.dts[:K], dJ_dp=dJ_dp, dJ_dslip=dJ_dslip)
+    k0 = np.asarray(prob.k, float)
+    f0 = prob.fault.f
+    for d in range(2):
+        vk = rng.normal(size=k0.size)
+        vf = rng.normal()
+        vq = rng.normal()
+        pred = g["g_logk"] @ vk + g["g_f"].sum() * vf + g["g_logQ"] * vq
+        h = 1e-5
+        J = []
+        for sgn in (1, -1):
+            _, tr = run_traj(prob, K, k=k0 * np.exp(sgn * h * vk), f=f0 + sgn * h * vf,
+                             qscale=math.exp(sgn * h * vq))
+            assert np.array_equal(tr[-1]["res"].flags, final.flags)
+            J.append(objective(tr[-1]["res"], obs_pairs, obs_nodes))
+        fd = (J[0] - J[1]) / (2 * h)
+        assert pred == pytest.approx(fd, rel=1e-5)
