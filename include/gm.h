@@ -273,6 +273,16 @@ int gm_adjoint_sweep_step(gm_ctx* ctx, const double* dJ_du_dev, const double* dJ
                           double* g_logk_dev, double* g_f_dev, double* g_logQ_host,
                           double rtol, int maxit, gm_solve_report* report_host, void* stream);
 
+/* Options of the adjoint solves (gm_adjoint_step, gm_adjoint_sweep_step).
+ * The Krylov iteration (flexible GMRES(30) on the transposed consistent
+ * Jacobian) always applies the operator in FP64; its preconditioner is one
+ * partitioned solve (Sec. 3.3.2) of the symmetric Newton system, inexact by
+ * design.  precision: GM_F64 (default) or GM_F32 for the preconditioner's
+ * inner operators; prec_rtol: relative tolerance of that solve (default 1e-8;
+ * values in (0, 1)); schur_precond: 0 or 1 as in gm_step_opts.  Returns
+ * GM_EINVAL for values out of range; the previous options are kept then. */
+int gm_set_adjoint_options(gm_ctx* ctx, int precision, double prec_rtol, int schur_precond);
+
 /* ---- state I/O (checkpoint / resume) --------------------------------- */
 
 /* Copy the accepted state to host arrays (any may be NULL): u (3N), p (N, tied

@@ -89,6 +89,7 @@ _SIG = {
     "gm_set_friction": (C.c_int, [_P, _D, C.c_int64]),
     "gm_adjoint_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _D, C.c_double, C.c_int,
                                   C.POINTER(SolveReport), _P]),
+    "gm_set_adjoint_options": (C.c_int, [_P, C.c_int, C.c_double, C.c_int]),
     "gm_adjoint_sweep_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _D,
                                         C.c_double, C.c_int, C.POINTER(SolveReport), _P]),
 }
@@ -349,6 +350,11 @@ class Solver:
         self._chk(self._L.gm_adjoint_step(self.h, ptr[0], ptr[1], ptr[2], _tptr(gk), _tptr(gf),
                                           C.byref(gq), rtol, maxit, C.byref(rep), _stream_ptr(stream)))
         return gk, gf[:self.P], gq.value, dict(iterations=rep.iterations, rel_residual=rep.rel_residual)
+
+    def set_adjoint_options(self, precision=F64, prec_rtol=1e-8, schur_precond=0):
+        """gm_set_adjoint_options: precision (F64/F32) and tolerance of the
+        adjoint solves' preconditioner, and its Schur preconditioner."""
+        self._chk(self._L.gm_set_adjoint_options(self.h, precision, prec_rtol, schur_precond))
 
     def adjoint_sweep_step(self, dJ_du=None, dJ_dp=None, dJ_dslip=None, lam_next=None,
                            mu_next=None, frozen_next=None, rtol=1e-10, maxit=300, stream=None):

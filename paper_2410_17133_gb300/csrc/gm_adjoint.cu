@@ -248,8 +248,8 @@ int apply_preconditioner(gm_ctx* c, const double* v, double* z, double prtol, in
     int oit = 0;
     long long ia = 0;
     double rr = 0;
-    int rc = gm_prevost(c, GM_F64, t, t + 3 * N, z, z + 3 * N, prtol, pmaxit, prtol * 1e-2, 20000, &oit,
-                        inner_k, &ia, &rr, s, 0);
+    int rc = gm_prevost(c, c->adj_prec, t, t + 3 * N, z, z + 3 * N, prtol, pmaxit, prtol * 1e-2, 20000, &oit,
+                        inner_k, &ia, &rr, s, c->adj_schur);
     if (rc && rc != GM_ENOCONV) return rc;
     adj_flip_p_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(N, z, z);
     GM_LAUNCHED(c);
@@ -269,6 +269,21 @@ extern "C" int gm_set_permeability(gm_ctx* c, const double* k, int64_t n)
         c->kperm[e] = v;
     }
     return gm_upload_permeability(c);
+}
+
+extern "C" int gm_set_adjoint_options(gm_ctx* c, int precision, double prec_rtol, int schur_precond)
+{
+    if (!c) return GM_EINVAL;
+    if (precision != GM_F64 && precision != GM_F32)
+        return c->set_err(GM_EINVAL, "set_adjoint_options: precision must be GM_F64 or GM_F32");
+    if (!(prec_rtol > 0 && prec_rtol < 1))
+        return c->set_err(GM_EINVAL, "set_adjoint_options: prec_rtol must lie in (0, 1)");
+    if (schur_precond != 0 && schur_precond != 1)
+        return c->set_err(GM_EINVAL, "set_adjoint_options: schur_precond must be 0 or 1");
+    c->adj_prec = precision;
+    c->adj_prtol = prec_rtol;
+    c->adj_schur = schur_precond;
+    return GM_OK;
 }
 
 extern "C" int gm_set_friction(gm_ctx* c, const double* f, int64_t n)
@@ -308,7 +323,7 @@ static int adj_solve(gm_ctx* c, double rtol, int maxit, gm_solve_report* rep, cu
     long long ik = 0;
     int it = 0;
     double res = beta0;
-    const double prtol = 1e-8;
+    const double prtol = c->adj_prtol;
     // flexible GMRES(m), right preconditioned; restart from r = b - A x
     while (beta0 > 0 && res > rtol * beta0 && it < maxit) {
         double* r = V;   // V[0]

@@ -260,6 +260,9 @@ struct gm_ctx {
     double Lref[64] = {};                              // nodal L of the reference cell (k/mu = 1)
     DevBuf adj_V, adj_Z, adj_w, adj_b, adj_x, adj_t;   // adjoint (FGMRES) work, allocated on first use
     int adj_m = 0;
+    int adj_prec = 0;            // preconditioner precision (GM_F64 / GM_F32)
+    double adj_prtol = 1e-8;     // preconditioner tolerance
+    int adj_schur = 0;           // preconditioner's Schur preconditioner
     DevBuf ddiagK, ddiagA, dKinv64, dKinv32, dAinv64, dAinv32;
     DevBuf dFS64, dFS32, dAfsinv64, dAfsinv32;         // fixed-stress storage term
     DevBuf dscal;                                      // PcgScalars[4] + misc
@@ -352,6 +355,12 @@ int gm_launch_axpby(gm_ctx* c, long long n, double a, const double* x, double b,
 int gm_launch_copy_cast_d2f(gm_ctx* c, long long n, const double* x, float* y, cudaStream_t s);
 int gm_launch_copy_cast_f2d(gm_ctx* c, long long n, const float* x, double* y, cudaStream_t s);
 int gm_launch_axpy_f2d(gm_ctx* c, long long n, double a, const float* x, double* y, cudaStream_t s);
+// scaled cast for the FP32 correction solves: sc (2 device doubles) receives
+// x.x and the power-of-two scale 2^e; y = x / 2^e, later y_64 += 2^e x_32
+int gm_launch_cast_scaled_d2f(gm_ctx* c, long long n, const double* x, float* y, double* sc,
+                              cudaStream_t s);
+int gm_launch_axpy_scaled_f2d(gm_ctx* c, long long n, const double* sc, const float* x, double* y,
+                              cudaStream_t s);
 // Deterministic dot products: out[0] = x.y (and out[1] = x2.y2 if x2) as doubles
 int gm_launch_dot(gm_ctx* c, long long n, const double* x, const double* y, const double* x2,
                   const double* y2, double* out, cudaStream_t s);

@@ -305,6 +305,45 @@ __global__ void gm_axpy_f2d_kernel(long long n, double a, const float* x, double
         y[i] += a * (double)x[i];
 }
 
+// y = x / 2^e in FP32, with 2^e the power of two at or below the RMS of x read
+// from sc[0] = x.x (e = 0 when x is zero or not finite); sc[1] = 2^e.  The FP32
+// correction solves then work on values of order one however small the Newton
+// residual has become, away from FP32 subnormals; the scale is exact.
+__global__ void gm_d2f_scaled_kernel(long long n, const double* x, float* y, double* sc)
+{
+    const double ms = sc[0] / (double)n;
+    const int e = (ms > 0.0 && isfinite(ms)) ? ilogb(sqrt(ms)) : 0;
+    const double inv = ldexp(1.0, -e);
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc[1] = ldexp(1.0, e);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = (float)(x[i] * inv);
+}
+__global__ void gm_axpy_f2d_scaled_kernel(long long n, const double* sc, const float* x, double* y)
+{
+    const double a = sc[1];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] += a * (double)x[i];
+}
+
+int gm_launch_cast_scaled_d2f(gm_ctx* c, long long n, const double* x, float* y, double* sc,
+                              cudaStream_t s)
+{
+    int rc = gm_launch_dot(c, n, x, x, nullptr, nullptr, sc, s);
+    if (rc) return rc;
+    gm_d2f_scaled_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(n, x, y, sc);
+    GM_LAUNCHED(c);
+    return GM_OK;
+}
+int gm_launch_axpy_scaled_f2d(gm_ctx* c, long long n, const double* sc, const float* x, double* y,
+                              cudaStream_t s)
+{
+    gm_axpy_f2d_scaled_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(n, sc, x, y);
+    GM_LAUNCHED(c);
+    return GM_OK;
+}
+
 int gm_launch_copy_cast_d2f(gm_ctx* c, long long n, const double* x, float* y, cudaStream_t s)
 {
     gm_d2f_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(n, x, y);

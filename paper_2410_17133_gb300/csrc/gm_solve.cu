@@ -65,17 +65,18 @@ int gm_pcg(gm_ctx* c, int which, int prec, const double* b, double* x, double rt
         q = (which == 0 ? c->k_q32 : c->a_q32).p;
         xx = (which == 0 ? c->k_x32 : c->a_x32).p;
         float* b32 = (which == 0 ? c->k_b32 : c->a_b32).as<float>();
+        double* bsc = reinterpret_cast<double*>(c->dscal.as<PcgScalars>() + 8 + which);
         // FP64 residual of the initial guess, then FP32 correction solve from 0
         if (x_zero) {
             GM_CUDA_TRY(c, cudaMemsetAsync(x, 0, n * sizeof(double), s));
-            if ((rc = gm_launch_copy_cast_d2f(c, n, b, b32, s))) return rc;
+            if ((rc = gm_launch_cast_scaled_d2f(c, n, b, b32, bsc, s))) return rc;
         } else {
             double* q64 = (which == 0 ? c->k_q : c->a_q).as<double>();
             if ((rc = apply_inner(c, which, GM_F64, x, q64, s, nullptr))) return rc;
             double* r64 = (which == 0 ? c->k_r : c->a_r).as<double>();
             GM_CUDA_TRY(c, cudaMemcpyAsync(r64, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
             if ((rc = gm_launch_axpby(c, n, -1.0, q64, 1.0, r64, s))) return rc;
-            if ((rc = gm_launch_copy_cast_d2f(c, n, r64, b32, s))) return rc;
+            if ((rc = gm_launch_cast_scaled_d2f(c, n, r64, b32, bsc, s))) return rc;
         }
         GM_CUDA_TRY(c, cudaMemsetAsync(xx, 0, n * sizeof(float), s));
         bb = b32;
@@ -149,7 +150,8 @@ int gm_pcg(gm_ctx* c, int which, int prec, const double* b, double* x, double rt
         if (batch < 32) batch *= 2;
     }
     if (prec != GM_F64) {
-        if ((rc = gm_launch_axpy_f2d(c, n, 1.0, (const float*)xx, x, s))) return rc;
+        const double* bsc = reinterpret_cast<const double*>(c->dscal.as<PcgScalars>() + 8 + which);
+        if ((rc = gm_launch_axpy_scaled_f2d(c, n, bsc, (const float*)xx, x, s))) return rc;
     } else {
         if ((rc = gm_launch_axpby(c, n, 1.0, (const double*)xx, 1.0, x, s))) return rc;
     }

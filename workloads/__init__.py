@@ -37,6 +37,8 @@ __all__ = [
     "fault_small",
     "slip_front",
     "inclined_lognormal",
+    "adjoint_lognormal",
+    "adjoint_objective",
     "column_terzaghi",
     "theis_plate",
     "tiny_faulted",
@@ -235,6 +237,35 @@ def inclined_lognormal(n: int = 160, steps: int = 20, seed: int = 3,
                    notes=f"seed={seed} dip={dip_deg}")
 
 
+def adjoint_lognormal(n: int = 64, steps: int = 20, seed: int = 4, Q: float = 2e-5,
+                      dt: float = 0.1) -> Problem:
+    """The unit-cube faulted case of ``fault_small`` on n^3 hexes with a
+    per-element log-normal permeability, log10 k ~ N(-15, 0.5) from numpy
+    default_rng(seed); E=20 GPa, nu=0.25, alpha=0.8, M=50 GPa, mu=1e-3 Pa s,
+    fault f=0.6, sigma'_n0=10 MPa, tau0=5.4 MPa, Table-1 fracture flow,
+    constant injection Q at the centre pair, ``steps`` steps of ``dt``.
+    The workload of gradient (adjoint) runs."""
+    prob = fault_small(n=n, Q=Q, steps=steps, dt=dt)
+    rng = np.random.default_rng(seed)
+    prob.k = 10.0 ** rng.normal(-15.0, 0.5, prob.n_el)
+    prob.name = f"adjoint{n}"
+    prob.notes = f"seed={seed} Q={Q} dt={dt}"
+    return prob
+
+
+def adjoint_objective(prob: Problem, n_slip: int = 256, n_p: int = 64, seed: int = 44):
+    """Observation sets of the gradient workload: ``n_slip`` random fault
+    pairs (slip observed) and ``n_p`` random bulk nodes (pressure observed),
+    from numpy default_rng(seed), without repetition."""
+    rng = np.random.default_rng(seed)
+    pairs = rng.choice(prob.n_pairs, min(n_slip, prob.n_pairs), replace=False)
+    nb = (prob.nx + 1) * (prob.ny + 1)
+    lo = nb * (prob.kf + 1)          # exclude both fault node planes
+    bulk = np.concatenate([np.arange(0, nb * prob.kf), np.arange(lo + nb, prob.n_nodes)])
+    nodes = rng.choice(bulk, min(n_p, bulk.size), replace=False)
+    return pairs, nodes
+
+
 def column_terzaghi(nz: int = 16, H: float = 1.0, load: float = 1e6, steps: int = 200,
                     dt: float = None, E: float = 20e9, nu: float = 0.25,
                     alpha: float = 0.8, M: float = 50e9, k: float = 1e-15,
@@ -340,4 +371,5 @@ CONFIGS = {
     "fault8": fault_small,
     "slipfront64": slip_front,
     "inclined160": inclined_lognormal,
+    "adjoint64": adjoint_lognormal,
 }
