@@ -225,7 +225,7 @@ int gm_residual_noalloc(gm_ctx* ctx, const double* du_dev, const double* dp_dev,
 int gm_partitioned_step(gm_ctx* ctx, double dt, const gm_step_opts* opts_host,
                         gm_step_report* report_host, void* stream);
 
-/* ---- parameters and adjoint (gradients) ------------------ */
+/* ---- parameters and adjoint (gradients) ------------------------------- */
 
 /* Replace the element permeabilities (n = n_el, or 1 to broadcast) without
  * resetting the state; diagonals are refreshed.  Synchronises. */

@@ -38,6 +38,9 @@ def return_map(jump, n, t1, t2, kn, ks, f, tn0, tau0, dlie_prev):
     jump      (P, 3) displacement jump [[u]] = u+ - u- in global axes
     n,t1,t2   (P, 3) local frame
     f         scalar or (P,) friction coefficient
+    tn0, tau0 in-situ effective normal traction (scalar or (P,)) and shear
+              traction in the frame (t1, t2) ((2,) or (P, 2)); depth-dependent
+              in-situ stress gives one value per pair
     dlie_prev (P, 2) inelastic slip at the last accepted step, frame (t1, t2)
     Returns dict with
       state (P,) int, tn (P,), ts (P, 2), dlie (P, 2), dlam (P,),
@@ -48,12 +51,13 @@ def return_map(jump, n, t1, t2, kn, ks, f, tn0, tau0, dlie_prev):
     jump = np.asarray(jump, float)
     P = jump.shape[0]
     f = np.broadcast_to(np.asarray(f, float), (P,))
-    tau0 = np.asarray(tau0, float)
+    tn0 = np.broadcast_to(np.asarray(tn0, float), (P,))
+    tau0 = np.broadcast_to(np.asarray(tau0, float), (P, 2))
     dn = np.sum(n * jump, axis=1)
     gs = np.stack([np.sum(t1 * jump, axis=1), np.sum(t2 * jump, axis=1)], axis=1)
     tn_c = tn0 - kn * dn                      # contact traction if the lips touch
     contact = tn_c >= 0.0
-    ttr = tau0[None, :] + ks * (gs - dlie_prev)
+    ttr = tau0 + ks * (gs - dlie_prev)
     nt = np.sqrt(np.sum(ttr * ttr, axis=1))
     tn = np.where(contact, tn_c, 0.0)
     F = nt - f * tn
@@ -78,8 +82,8 @@ def return_map(jump, n, t1, t2, kn, ks, f, tn0, tau0, dlie_prev):
     Tn = np.where(contact, kn * dn, tn0)
     Ts = np.zeros((P, 2))
     Ts[stick] = ks * (gs[stick] - dlie_prev[stick])
-    Ts[slip] = ts[slip] - tau0[None, :]
-    Ts[state == OPEN] = -tau0[None, :]
+    Ts[slip] = ts[slip] - tau0[slip]
+    Ts[state == OPEN] = -tau0[state == OPEN]
     T = Tn[:, None] * n + Ts[:, 0:1] * t1 + Ts[:, 1:2] * t2
 
     nn = np.einsum("pi,pj->pij", n, n)

@@ -101,7 +101,10 @@ def insitu_floor(model: Model):
         return 0.0
     fg = model.fg
     fp = model.prob.fault
-    F0 = (-fp.tn0 * fg["n"] + fp.tau0[0] * fg["t1"] + fp.tau0[1] * fg["t2"]) * fg["area"][:, None]
+    P = fg["n"].shape[0]
+    tn0 = np.broadcast_to(np.asarray(fp.tn0, float), (P,))[:, None]
+    tau0 = np.broadcast_to(np.asarray(fp.tau0, float), (P, 2))
+    F0 = (-tn0 * fg["n"] + tau0[:, 0:1] * fg["t1"] + tau0[:, 1:2] * fg["t2"]) * fg["area"][:, None]
     N = model.N
     tot = 0.0
     for lip in (fg["pairs"][:, 0], fg["pairs"][:, 1]):

@@ -94,3 +94,24 @@ def test_tangent_stick_exact_and_slip_symmetric_reading():
     assert np.allclose(r["D"][0] - f * kn * np.outer(taug, n[0]), fd_jac(j), rtol=1e-5, atol=1e-5)
     assert np.allclose(r["D"][0], r["D"][0].T)
     assert np.all(rm([0, 0, 0.05])["D"][0] == 0.0)
+
+
+def test_per_pair_insitu_equals_pairwise_scalar_calls():
+    """Per-pair in-situ tractions (depth-dependent stress) give, pair by pair,
+    the result of the pinned single-pair law with that pair's scalars."""
+    rng = np.random.default_rng(11)
+    P = 9
+    nn = np.repeat(n, P, 0)
+    tt1 = np.repeat(t1, P, 0)
+    tt2 = np.repeat(t2, P, 0)
+    tn0p = rng.uniform(5.0, 15.0, P)
+    tau0p = np.stack([rng.uniform(1.0, 6.0, P), rng.uniform(-1.0, 1.0, P)], 1)
+    jump = np.stack([rng.uniform(-0.05, 0.05, P), rng.uniform(-0.05, 0.05, P),
+                     rng.uniform(-0.004, 0.02, P)], 1)
+    dlie = rng.uniform(-0.01, 0.01, (P, 2))
+    r = return_map(jump, nn, tt1, tt2, kn, ks, f, tn0p, tau0p, dlie)
+    assert len(set(r["state"].tolist())) == 3          # open, stick and slip all present
+    for i in range(P):
+        ri = return_map(jump[i:i + 1], n, t1, t2, kn, ks, f, tn0p[i], tau0p[i], dlie[i:i + 1])
+        for key in ("state", "tn", "ts", "dlie", "T", "D", "F"):
+            assert np.array_equal(r[key][i], ri[key][0]), (i, key)
