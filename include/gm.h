@@ -236,6 +236,17 @@ int gm_set_permeability(gm_ctx* ctx, const double* k_host, int64_t n);
  * return map.  Synchronises. */
 int gm_set_friction(gm_ctx* ctx, const double* f_host, int64_t n);
 
+/* Per-pair in-situ fault tractions, for in-situ stress that varies over the
+ * fault (depth gradients, Sec. 5): tn0_host[i] is the effective normal
+ * traction t'_n0 of pair i (compression > 0) and tau0_host the shear traction
+ * in the fault frame, field-major (tau0_1 of all pairs, then tau0_2); n is the
+ * pair count.  They replace the uniform tn0, tau0 of gm_fault_plane in the
+ * return map (Sec. 2.2.1: the in-situ tractions are the offsets of the
+ * elastic predictor) and in the Newton test's scale; both NULL restores the
+ * uniform values.  Valid after gm_assemble_or_bind, which clears them.
+ * GM_EINVAL for a wrong n, one NULL array or non-finite values.  Synchronises. */
+int gm_set_insitu(gm_ctx* ctx, const double* tn0_host, const double* tau0_host, int64_t n);
+
 /* Adjoint of the last converged implicit step (call it right after
  * gm_partitioned_step, before anything re-runs the return map).  For an
  * objective J(u, p) whose derivatives the caller gives as device vectors

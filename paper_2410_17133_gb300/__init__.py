@@ -90,6 +90,7 @@ _SIG = {
     "gm_adjoint_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _D, C.c_double, C.c_int,
                                   C.POINTER(SolveReport), _P]),
     "gm_set_adjoint_options": (C.c_int, [_P, C.c_int, C.c_double, C.c_int]),
+    "gm_set_insitu": (C.c_int, [_P, _P, _P, C.c_int64]),
     "gm_adjoint_sweep_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _D,
                                         C.c_double, C.c_int, C.POINTER(SolveReport), _P]),
 }
@@ -174,6 +175,16 @@ class Solver:
         fp = FaultParams(kn, ks, f, w0, wk_par, k_perp, MF, tn0, (C.c_double * 2)(*tau0))
         self._chk(self._L.gm_fault_plane(self.h, int(kf), C.byref(fp)))
 
+    def set_insitu(self, tn0=None, tau0=None):
+        """gm_set_insitu: per-pair in-situ tractions, tn0 (P,) and tau0 (P, 2) in
+        the fault frame (t1, t2); None for both restores the uniform values."""
+        if tn0 is None and tau0 is None:
+            self._chk(self._L.gm_set_insitu(self.h, None, None, self.P))
+            return
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(tn0, np.float64), (self.P,)))
+        b = np.ascontiguousarray(np.broadcast_to(np.asarray(tau0, np.float64), (self.P, 2)).T)
+        self._chk(self._L.gm_set_insitu(self.h, _dptr(a), _dptr(b), self.P))
+
     def materials(self, E, k, nu, alpha, M, mu_f):
         E = np.ascontiguousarray(np.atleast_1d(E), np.float64)
         k = np.ascontiguousarray(np.broadcast_to(np.atleast_1d(k), E.shape), np.float64)
@@ -207,13 +218,17 @@ class Solver:
         s.mesh(prob.nx, prob.ny, prob.nz, prob.origin, prob.h, prob.shear)
         if prob.kf is not None:
             fp = prob.fault
-            s.fault(prob.kf, fp.kn, fp.ks, fp.f, fp.w0, fp.wk_par, fp.k_perp, fp.MF, fp.tn0, fp.tau0)
+            per_pair = np.ndim(fp.tn0) > 0 or np.ndim(fp.tau0) > 1
+            s.fault(prob.kf, fp.kn, fp.ks, fp.f, fp.w0, fp.wk_par, fp.k_perp, fp.MF,
+                    float(np.mean(fp.tn0)), np.mean(np.reshape(fp.tau0, (-1, 2)), axis=0))
         E = np.asarray(prob.E, np.float64)
         s.materials(E, np.broadcast_to(np.asarray(prob.k, np.float64), E.shape), prob.nu, prob.alpha,
                     prob.M, prob.mu_f)
         s.dirichlet(prob.fixed)
         s.loads(prob.fu, prob.fp)
         s.bind()
+        if prob.kf is not None and per_pair:
+            s.set_insitu(fp.tn0, fp.tau0)
         return s
 
     # -- operators -------------------------------------------------------------

@@ -95,11 +95,14 @@ __global__ void gm_return_map_kernel(const LawArgs a)
     const double g1 = a.t1[0] * j[0] + a.t1[1] * j[1] + a.t1[2] * j[2];
     const double g2 = a.t2[0] * j[0] + a.t2[1] * j[1] + a.t2[2] * j[2];
     const double fr = a.fpair ? a.fpair[i] : a.f;
-    const double tnc = a.tn0 - a.kn * dn;
+    const double tn0 = a.insitu ? a.insitu[i] : a.tn0;
+    const double t01 = a.insitu ? a.insitu[P + i] : a.tau0[0];
+    const double t02 = a.insitu ? a.insitu[2 * P + i] : a.tau0[1];
+    const double tnc = tn0 - a.kn * dn;
     const bool contact = tnc >= 0.0;
     const double dl1 = a.dlie_prev[i], dl2 = a.dlie_prev[P + i];
-    const double tr1 = a.tau0[0] + a.ks * (g1 - dl1);
-    const double tr2 = a.tau0[1] + a.ks * (g2 - dl2);
+    const double tr1 = t01 + a.ks * (g1 - dl1);
+    const double tr2 = t02 + a.ks * (g2 - dl2);
     const double nt = sqrt(tr1 * tr1 + tr2 * tr2);
     const double tn = contact ? tnc : 0.0;
     const double F = nt - fr * tn;
@@ -116,14 +119,14 @@ __global__ void gm_return_map_kernel(const LawArgs a)
         const double dlam = F / a.ks;
         ts1 = fr * tn * tau1; ts2 = fr * tn * tau2;
         l1 = dl1 + dlam * tau1; l2 = dl2 + dlam * tau2;
-        Ts1 = ts1 - a.tau0[0];
-        Ts2 = ts2 - a.tau0[1];
+        Ts1 = ts1 - t01;
+        Ts2 = ts2 - t02;
         ratio = fr * tn / nt;
     } else {
-        Ts1 = -a.tau0[0];
-        Ts2 = -a.tau0[1];
+        Ts1 = -t01;
+        Ts2 = -t02;
     }
-    const double Tn = contact ? a.kn * dn : a.tn0;
+    const double Tn = contact ? a.kn * dn : tn0;
     a.state[i] = contact ? (slip ? GM_SLIP : GM_STICK) : GM_OPEN;
     a.tn[i] = tn;
     a.ts[i] = ts1; a.ts[P + i] = ts2;
@@ -171,6 +174,7 @@ int gm_launch_return_map(gm_ctx* c, const double* un, const double* du, cudaStre
     a.du = du;
     a.dlie_prev = c->ddlie_n.as<double>();
     a.fpair = c->has_fpair ? c->dfpair.as<double>() : nullptr;
+    a.insitu = c->has_insitu ? c->dinsitu.as<double>() : nullptr;
     a.tauc = c->dtauc.as<double>();
     a.kn = c->fp.kn; a.ks = c->fp.ks; a.f = c->fp.f; a.tn0 = c->fp.tn0;
     a.tau0[0] = c->fp.tau0[0]; a.tau0[1] = c->fp.tau0[1];

@@ -290,6 +290,60 @@ int gm_mesh_structured(gm_ctx* c, int nx, int ny, int nz, const double* origin, 
     return GM_OK;
 }
 
+// Floor of the Newton test from the in-situ fault forces: sum of F0^2 / diag(K_b)
+// over free lip dofs, F0 = A_i (-t'_n0 n + tau0) with per-pair values if set.
+static int gm_insitu_floor(gm_ctx* c)
+{
+    c->f0sq = 0.0;
+    if (!c->has_fault) return GM_OK;
+    const long long N = c->N, N3 = 3 * N;
+    std::vector<double> dK(N3);
+    GM_CUDA_TRY(c, cudaMemcpy(dK.data(), c->ddiagK.p, N3 * 8, cudaMemcpyDeviceToHost));
+    const long long nb = c->g.nb;
+    for (long long q = 0; q < nb; ++q) {
+        const int pi = (int)(q % (c->nx + 1)), pj = (int)(q / (c->nx + 1));
+        const int nqi = (pi > 0) + (pi < c->nx), nqj = (pj > 0) + (pj < c->ny);
+        const double Ai = c->Aq * 0.25 * nqi * nqj;
+        const double tn0 = c->has_insitu ? c->h_insitu[q] : c->fp.tn0;
+        const double t01 = c->has_insitu ? c->h_insitu[nb + q] : c->fp.tau0[0];
+        const double t02 = c->has_insitu ? c->h_insitu[2 * nb + q] : c->fp.tau0[1];
+        for (int lip = 0; lip < 2; ++lip) {
+            const long long n = q + nb * (c->g.kf + lip);
+            for (int d = 0; d < 3; ++d) {
+                if (c->fixed[d * N + n]) continue;
+                const double F0 = Ai * (-tn0 * c->nrm[d] + t01 * c->t1[d] + t02 * c->t2[d]);
+                c->f0sq += F0 * F0 / dK[d * N + n];
+            }
+        }
+    }
+    return GM_OK;
+}
+
+int gm_set_insitu(gm_ctx* c, const double* tn0, const double* tau0, int64_t n)
+{
+    if (!c) return GM_EINVAL;
+    if (!c->bound || !c->has_fault) return c->set_err(GM_ESTATE, "set_insitu: needs a bound fault");
+    if (!tn0 && !tau0) {
+        c->has_insitu = false;
+        c->h_insitu.clear();
+        return gm_insitu_floor(c);
+    }
+    if (!tn0 || !tau0) return c->set_err(GM_EINVAL, "set_insitu: give both arrays, or neither");
+    if (n != c->P) return c->set_err(GM_EINVAL, "set_insitu: n must be the pair count");
+    std::vector<double> h((size_t)3 * n);
+    for (long long i = 0; i < n; ++i) {
+        if (!std::isfinite(tn0[i]) || !std::isfinite(tau0[i]) || !std::isfinite(tau0[n + i]))
+            return c->set_err(GM_EINVAL, "set_insitu: values must be finite");
+        h[i] = tn0[i];
+        h[n + i] = tau0[i];
+        h[2 * n + i] = tau0[n + i];
+    }
+    GM_CUDA_TRY(c, cudaMemcpy(c->dinsitu.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice));
+    c->h_insitu.swap(h);
+    c->has_insitu = true;
+    return gm_insitu_floor(c);
+}
+
 int gm_fault_plane(gm_ctx* c, int kf, const gm_fault_params* p)
 {
     if (!c) return GM_EINVAL;
@@ -648,7 +702,8 @@ extern "C" int gm_partitioned_step(gm_ctx* c, double dt, const gm_step_opts* opt
             else if (st[i] == GM_STICK) R.n_stick++;
             else R.n_slip++;
             if (tn[i] > 0) ym = std::min(ym, std::fabs(F[i]) / (c->fp.f * tn[i]));
-            nm = std::min(nm, std::fabs(c->fp.tn0 - c->fp.kn * dn[i]) / c->fp.tn0);
+            const double tn0 = c->has_insitu ? c->h_insitu[i] : c->fp.tn0;
+            nm = std::min(nm, std::fabs(tn0 - c->fp.kn * dn[i]) / tn0);
         }
         R.min_yield_margin = ym;
         R.min_normal_margin = nm;
@@ -762,6 +817,8 @@ int bind_impl(gm_ctx* c)
     for (int a = 0; a < 8; ++a)
         for (int b = 0; b < 8; ++b) c->Lref[8 * a + b] = L[a][b];
     c->has_fpair = false;
+    c->has_insitu = false;
+    c->h_insitu.clear();
     c->fault_cons = 0;
     c->adj_m = 0;
     for (DevBuf* bf : {&c->adj_V, &c->adj_Z, &c->adj_w, &c->adj_b, &c->adj_x, &c->adj_t}) bf->release();
@@ -839,6 +896,7 @@ int bind_impl(gm_ctx* c)
         {&c->dF, (size_t)P * 8}, {&c->ddn, (size_t)P * 8}, {&c->dgs, (size_t)2 * P * 8},
         {&c->dD64, (size_t)6 * P * 8}, {&c->dD32, (size_t)6 * P * 4},
         {&c->dtauc, (size_t)4 * P * 8}, {&c->dfpair, (size_t)P * 8},
+        {&c->dinsitu, (size_t)3 * P * 8},
         {&c->ddiagK, (size_t)N3 * 8}, {&c->ddiagA, (size_t)N * 8},
         {&c->dKinv64, (size_t)12 * N * 8}, {&c->dKinv32, (size_t)6 * N * 4},
         {&c->dAinv64, (size_t)N * 8}, {&c->dAinv32, (size_t)N * 4},
@@ -912,26 +970,8 @@ int bind_impl(gm_ctx* c)
     }
     if ((rc = gm_launch_block_jacobi(c, 0))) { c->bound = false; return rc; }
     GM_CUDA_TRY(c, cudaDeviceSynchronize());
-    // in-situ fault force floor for the Newton test: sum F0^2 / diag(K_b), free lip dofs
-    c->f0sq = 0.0;
-    if (c->has_fault) {
-        std::vector<double> dK(N3);
-        GM_CUDA_TRY(c, cudaMemcpy(dK.data(), c->ddiagK.p, N3 * 8, cudaMemcpyDeviceToHost));
-        const long long nb = c->g.nb;
-        for (long long q = 0; q < nb; ++q) {
-            const int pi = (int)(q % (c->nx + 1)), pj = (int)(q / (c->nx + 1));
-            const int nqi = (pi > 0) + (pi < c->nx), nqj = (pj > 0) + (pj < c->ny);
-            const double Ai = c->Aq * 0.25 * nqi * nqj;
-            for (int lip = 0; lip < 2; ++lip) {
-                const long long n = q + nb * (c->g.kf + lip);
-                for (int d = 0; d < 3; ++d) {
-                    if (c->fixed[d * N + n]) continue;
-                    const double F0 = Ai * (-c->fp.tn0 * c->nrm[d] + c->fp.tau0[0] * c->t1[d] + c->fp.tau0[1] * c->t2[d]);
-                    c->f0sq += F0 * F0 / dK[d * N + n];
-                }
-            }
-        }
-    }
+    // in-situ fault force floor for the Newton test
+    if (int rc = gm_insitu_floor(c)) return rc;
     c->applies = 0;
     c->launches = 0;
     return GM_OK;

@@ -175,6 +175,7 @@ struct LawArgs {
     const double* du;        // increment (3N) or null
     const double* dlie_prev; // 2P
     const double* fpair;     // per-pair friction or null
+    const double* insitu;    // per-pair t'_n0, tau0_1, tau0_2 (3P, field-major) or null
     double kn, ks, f, tn0, tau0[2];
     double n[3], t1[3], t2[3];
     double Aq;
@@ -256,6 +257,9 @@ struct gm_ctx {
     DevBuf dstate, dtn, dts, ddlie, dT, dF, ddn, dgs, dD64, dD32;   // fault work
     DevBuf dtauc, dfpair;                              // consistent-tangent term, per-pair f
     bool has_fpair = false;
+    DevBuf dinsitu;                                    // per-pair in-situ tractions (3P)
+    bool has_insitu = false;
+    std::vector<double> h_insitu;                      // host copy (3P)
     int fault_cons = 0;                                // tangent variant used by the fault kernel
     double Lref[64] = {};                              // nodal L of the reference cell (k/mu = 1)
     DevBuf adj_V, adj_Z, adj_w, adj_b, adj_x, adj_t;   // adjoint (FGMRES) work, allocated on first use

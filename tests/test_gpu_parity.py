@@ -244,3 +244,50 @@ def test_implicit_steps_fp32_refined(name, steps):
         assert rel(st["u"], r.u) < 1e-8, (k, rel(st["u"], r.u))
         assert rel(st["p"], r.p) < 1e-8, (k, rel(st["p"], r.p))
         assert np.array_equal(st["flags"].astype(np.int64), r.flags), k
+
+
+def insitu_varying_case():
+    """fault_small on 6^3 with in-situ tractions that vary over the fault, as
+    depth-dependent stress makes them: t'_n0 from 8 to 12 MPa along x, tau0_1
+    from 4.9 to 5.9 MPa along y, a small tau0_2 that changes sign."""
+    import dataclasses
+    prob = W.fault_small(n=6, Q=5e-5, steps=3)
+    n = prob.nx
+    i = np.arange(prob.n_pairs) % (n + 1) / n
+    j = np.arange(prob.n_pairs) // (n + 1) / n
+    tn0 = 10e6 * (0.8 + 0.4 * i)
+    tau0 = np.stack([5.4e6 * (0.9 + 0.2 * j), 0.3e6 * (i - 0.5)], 1)
+    prob.fault = dataclasses.replace(prob.fault, tn0=tn0, tau0=tau0)
+    return prob
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_implicit_steps_per_pair_insitu(precision):
+    """gm_set_insitu: per-pair in-situ tractions give the oracle's steps (FP64
+    1e-9, FP32-refined 1e-8) with identical fault states; clearing them
+    restores the uniform-traction solver."""
+    need_gpu()
+    prob = insitu_varying_case()
+    s = solver_for(prob)
+    model, ref = osolve.run(prob, nsteps=3, rtol=1e-12)
+    tol = 1e-9 if precision == 0 else 1e-8
+    for k in range(3):
+        s.step(prob.dts[k], newton_rtol=1e-12, precision=precision)
+        st = s.get_state()
+        r = ref[k]
+        assert np.array_equal(st["flags"].astype(np.int64), r.flags), k
+        assert rel(st["u"], r.u) < tol, (k, rel(st["u"], r.u))
+        assert rel(st["p"], r.p) < tol
+        assert rel(st["slip"].T, r.slip) < tol
+    assert (r.flags == 2).sum() >= 10 and (r.flags == 1).sum() >= 10
+    # back to the uniform values of the fault parameters
+    s.set_insitu(None, None)
+    uni = W.fault_small(n=6, Q=5e-5, steps=3)
+    s2 = solver_for(uni)
+    s.set_state(u=np.zeros((3, s.N)), p=np.zeros(s.N), dlie=np.zeros((2, s.P)),
+                flags=np.ones(s.P, np.int8))
+    for k in range(2):
+        s.step(uni.dts[k], newton_rtol=1e-12, precision=precision)
+        s2.step(uni.dts[k], newton_rtol=1e-12, precision=precision)
+    a, b = s.get_state(), s2.get_state()
+    assert rel(a["u"], b["u"]) < 1e-12 and np.array_equal(a["flags"], b["flags"])
