@@ -1,4 +1,5 @@
-"""Full-size parity at the bench workloads (64^3 slip-front, 160^3 inclined):
+"""Full-size parity at the bench workloads (64^3 slip-front, 160^3 inclined,
+the 128x256x256 faulted aquifer):
 the GPU applies, in the launch configuration the bench uses, are compared with
 the oracle on sampled rows that the oracle evaluates from the elements around
 each sampled node (too large to assemble whole).  The implicit step at 64^3 is
@@ -26,10 +27,11 @@ def sample_nodes(prob, seed, k=400):
     return np.unique(np.concatenate(picks))
 
 
-@pytest.mark.parametrize("cfg", ["slipfront64", "inclined160"])
+@pytest.mark.parametrize("cfg", ["slipfront64", "inclined160", "aquifer"])
 def test_fullsize_sampled_apply(cfg):
     need_gpu()
-    prob = W.slip_front(n=64) if cfg == "slipfront64" else W.inclined_lognormal(n=160)
+    prob = {"slipfront64": lambda: W.slip_front(n=64), "inclined160": lambda: W.inclined_lognormal(n=160),
+            "aquifer": lambda: W.faulted_aquifer()}[cfg]()
     dt = prob.dts[0]
     s = solver_for(prob)
     s.timestep(dt)

@@ -1,0 +1,34 @@
+"""The seeded workload generators agree with the oracle's geometry: the
+faulted-aquifer workload projects its in-situ stress on the same fault frame
+(n, t1, t2) that the oracle (and the library) build from the grid, its line
+source injects exactly Q, and its layers are where they are stated."""
+import numpy as np
+
+import workloads as W
+from oracle import fem
+
+
+def test_faulted_aquifer_frame_source_and_layers():
+    p = W.faulted_aquifer(nv=20, ny=6, nz=8, steps=1, Q=0.5)
+    mesh = fem.Mesh(p.nx, p.ny, p.nz, p.origin, p.h, p.shear, p.kf)
+    fg = fem.fault_geometry(mesh)
+    # rebuild the tractions from the oracle's frame and a stress tensor with the
+    # stated gradients: they must equal the workload's
+    depth = 500.0 + 2000.0 - (np.arange(p.n_pairs) % (p.nx + 1)) * p.h[0]
+    p0 = 9.81e3 * depth
+    S = np.zeros((p.n_pairs, 3, 3))
+    S[:, 0, 0] = -(18.75e3 * depth - p0)
+    S[:, 1, 1] = -(20.4e3 * depth - p0)
+    S[:, 2, 2] = -(11.9e3 * depth - p0)
+    tr = np.einsum("pij,pj->pi", S, fg["n"])
+    assert np.allclose(-np.sum(tr * fg["n"], 1), p.fault.tn0, rtol=1e-12)
+    assert np.allclose(np.sum(tr * fg["t1"], 1), p.fault.tau0[:, 0], rtol=1e-12, atol=1e-6)
+    assert np.allclose(np.sum(tr * fg["t2"], 1), p.fault.tau0[:, 1], atol=1e-6)
+    # normal faulting: the footwall (+ side) carries shear up-dip, i.e. the
+    # hanging wall is driven down; everywhere 0.85 of the frictional strength
+    assert np.all(p.fault.tau0[:, 0] > 0)
+    assert np.allclose(np.hypot(*p.fault.tau0.T) / (0.6 * p.fault.tn0), 0.85, rtol=1e-3)
+    assert np.isclose(p.fp.sum(), 0.5)
+    assert np.unique(p.E).tolist() == [15e9, 25e9, 40e9]
+    k_aq = p.k[p.E == 15e9]
+    assert k_aq.min() > 1e-16 and p.k[p.E == 25e9].max() == 1e-19

@@ -39,6 +39,7 @@ __all__ = [
     "inclined_lognormal",
     "adjoint_lognormal",
     "adjoint_objective",
+    "faulted_aquifer",
     "column_terzaghi",
     "theis_plate",
     "tiny_faulted",
@@ -266,6 +267,85 @@ def adjoint_objective(prob: Problem, n_slip: int = 256, n_p: int = 64, seed: int
     return pairs, nodes
 
 
+def faulted_aquifer(nv: int = 128, ny: int = 256, nz: int = 256, steps: int = 100, seed: int = 5,
+                    dt: float = 43200.0, Q: float = 0.01, throw: float = 150.0,
+                    dip_deg: float = 80.0, sv_grad: float = 18.75e3) -> Problem:
+    """Faulted aquifer (Sec. 5 restated): 2000 m (vertical) x 4000 m x 4000 m.
+
+    Grid axes: x is vertical (x = 0 at the bottom, H = 2000 m at the top, nv
+    cells), y is the fault strike (ny cells), z crosses the fault (nz cells).
+    The affine map z_phys = z + tan(90 deg - dip) x tilts the fault node plane
+    kf = nz / 2 to the stated dip (80 deg: a mild 10 deg shear of the cells).
+    Three layers by height: basement (E = 40 GPa, k = 1e-18 m^2), aquifer
+    (E = 15 GPa, log10 k ~ N(-13, 0.7) from numpy default_rng(seed)) and
+    caprock (E = 25 GPa, k = 1e-19 m^2); the aquifer spans 950-1050 m on the
+    footwall and sits `throw` lower on the hanging wall (the grid-z < kf side,
+    above the dipping plane), so the two segments meet only through the fault.
+    nu = 0.15, alpha = 0.64, M = 22.7 GPa, mu = 0.89 mPa s; fault f = 0.6,
+    kn = 27300 GPa/m, ks = 273 GPa/m, Table-1 fracture flow, tied lip pressures.
+    In-situ stress grows with depth d below the ground surface (500 m of rock
+    above the model top): vertical sv_grad * d, horizontal 11.9 kPa/m * d across
+    the fault and 20.4 kPa/m * d along strike, hydrostatic pore pressure
+    9.81 kPa/m * d; the fault carries the effective traction of that stress per
+    pair, t'_n0 = -n.S'n and tau0 = (t1.S'n, t2.S'n) with S' the tension-positive
+    effective stress and (n, t1, t2) the library's fault frame (n from the
+    grid-z < kf side to the other, t1 the unit grid-x direction in the plane,
+    t2 = n x t1).  Injection Q as a line source over the hanging-wall aquifer at
+    mid-strike, 250 m from the fault, split by nodal length.  Bottom face
+    u = 0, all faces no-flow."""
+    H, Ly, Lz = 2000.0, 4000.0, 4000.0
+    nx = nv
+    kf = nz // 2
+    hx, hy, hz = H / nx, Ly / ny, Lz / nz
+    sx = math.tan(math.radians(90.0 - dip_deg))
+    fixed, fu, fp = _empty(nx, ny, nz, kf)
+    # bottom face: grid x = 0, every extended plane
+    nb = (nx + 1) * (ny + 1)
+    planes = n_planes(nz, kf)
+    bottom = (np.arange(ny + 1)[:, None] * (nx + 1) + nb * np.arange(planes)[None, :]).ravel()
+    fixed[0:3, bottom] = 1
+    # layers by element-centre height; hanging wall (k < kf) thrown down
+    ex = (np.arange(nx) + 0.5) * hx
+    nel = nx * ny * nz
+    zc = np.broadcast_to(ex[None, None, :], (nz, ny, nx)).reshape(-1)
+    kk = np.broadcast_to(np.arange(nz)[:, None, None], (nz, ny, nx)).reshape(-1)
+    lo = np.where(kk < kf, 950.0 - throw, 950.0)
+    layer = np.where(zc < lo, 0, np.where(zc < lo + 100.0, 1, 2))
+    rng = np.random.default_rng(seed)
+    k_aq = 10.0 ** rng.normal(-13.0, 0.7, nel)
+    E = np.choose(layer, [40e9, 15e9, 25e9])
+    k = np.choose(layer, [np.full(nel, 1e-18), k_aq, np.full(nel, 1e-19)])
+    # per-pair in-situ effective traction on the fault
+    n_ = np.array([-sx, 0.0, 1.0]) / math.hypot(sx, 1.0)
+    t1 = np.array([1.0, 0.0, sx]) / math.hypot(sx, 1.0)
+    t2 = np.cross(n_, t1)
+    P = nb
+    xi = (np.arange(P) % (nx + 1)) * hx
+    depth = 500.0 + H - xi
+    p0 = 9.81e3 * depth
+    S = np.zeros((P, 3, 3))            # tension-positive effective stress, physical axes
+    S[:, 0, 0] = -(sv_grad * depth - p0)
+    S[:, 1, 1] = -(20.4e3 * depth - p0)
+    S[:, 2, 2] = -(11.9e3 * depth - p0)
+    tr = S @ n_
+    tn0 = -(tr @ n_)
+    tau0 = np.stack([tr @ t1, tr @ t2], 1)
+    # line source over the hanging-wall aquifer
+    kw = kf - max(1, int(round(250.0 / hz)))
+    jw = ny // 2
+    top = 950.0 - throw + 100.0
+    iw = np.array([i for i in range(nx + 1) if 950.0 - throw - 1e-9 <= i * hx <= top + 1e-9])
+    w = np.full(iw.size, hx)
+    w[0] = w[-1] = 0.5 * hx
+    fp[iw + (nx + 1) * (jw + (ny + 1) * kw)] = Q * w / w.sum()
+    fault = FaultParams(kn=2.73e13, ks=2.73e11, f=0.6, w0=1e-4, wk_par=1e-15, k_perp=0.0,
+                        MF=0.2e6, tn0=tn0, tau0=tau0)
+    return Problem(name=f"aquifer{nv}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, origin=(0.0, 0.0, -Lz / 2),
+                   h=(hx, hy, hz), shear=(sx, 0.0), kf=kf, fault=fault, E=E, k=k, nu=0.15,
+                   alpha=0.64, M=22.7e9, mu_f=0.89e-3, fixed=fixed, fu=fu, fp=fp,
+                   dts=[dt] * steps, notes=f"seed={seed} dip={dip_deg} throw={throw}")
+
+
 def column_terzaghi(nz: int = 16, H: float = 1.0, load: float = 1e6, steps: int = 200,
                     dt: float = None, E: float = 20e9, nu: float = 0.25,
                     alpha: float = 0.8, M: float = 50e9, k: float = 1e-15,
@@ -371,5 +451,6 @@ CONFIGS = {
     "fault8": fault_small,
     "slipfront64": slip_front,
     "inclined160": inclined_lognormal,
+    "aquifer": faulted_aquifer,
     "adjoint64": adjoint_lognormal,
 }
