@@ -470,6 +470,62 @@ __global__ void __launch_bounds__(256) gm_block_jacobi_kernel(const BJArgs a)
     }
 }
 
+// 6x6 block of a fault pair: both lips' 3x3 blocks (bulk + A_i D) and the
+// coupling -A_i D between them.  The cohesive springs are stiff (k_n h / E of
+// order 10-1000), so the two lips move nearly together and a preconditioner
+// that inverts only nodal blocks cannot see that; the pair block does.
+// Constrained components: zero row and column (z = 0 there).  The block is
+// symmetric positive definite, so Gauss-Jordan without pivoting is stable.
+__global__ void __launch_bounds__(128) gm_pair_block_kernel(const BJArgs a, double* pinv64, float* pinv32)
+{
+    const long long P = a.g.nb;
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= P) return;
+    const long long N = a.g.N;
+    const long long nm = q + P * a.g.kf, np = nm + P;
+    const int i = (int)(q % (a.g.nx + 1)), j = (int)(q / (a.g.nx + 1));
+    const int nqi = (i > 0) + (i < a.g.nx), nqj = (j > 0) + (j < a.g.ny);
+    const double Ai = a.Aq * 0.25 * nqi * nqj;
+    double M[6][6];
+    const int sr[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};   // symmetric 3x3 storage
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double C = Ai * a.D[sr[r][c] * P + q];
+            M[r][c] = a.Kb6[sr[r][c] * N + nm] + C;
+            M[3 + r][3 + c] = a.Kb6[sr[r][c] * N + np] + C;
+            M[r][3 + c] = -C;
+            M[3 + r][c] = -C;
+        }
+    const unsigned mk = (a.mask[nm] & 7u) | ((a.mask[np] & 7u) << 3);
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+        if ((mk >> r) & 1u)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) { M[r][c] = (r == c) ? 1.0 : 0.0; M[c][r] = (r == c) ? 1.0 : 0.0; }
+    double I[6][6];
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) I[r][c] = (r == c) ? 1.0 : 0.0;
+    for (int k = 0; k < 6; ++k) {
+        const double piv = 1.0 / M[k][k];
+        for (int c = 0; c < 6; ++c) { M[k][c] *= piv; I[k][c] *= piv; }
+        for (int r = 0; r < 6; ++r) {
+            if (r == k) continue;
+            const double f = M[r][k];
+            for (int c = 0; c < 6; ++c) { M[r][c] -= f * M[k][c]; I[r][c] -= f * I[k][c]; }
+        }
+    }
+    for (int r = 0; r < 6; ++r)
+        for (int c = 0; c < 6; ++c) {
+            const double v = (((mk >> r) | (mk >> c)) & 1u) ? 0.0 : I[r][c];
+            pinv64[(r * 6 + c) * P + q] = v;
+            pinv32[(r * 6 + c) * P + q] = (float)v;
+        }
+}
+
 int gm_launch_block_jacobi(gm_ctx* c, cudaStream_t s)
 {
     BJArgs a;
@@ -483,6 +539,11 @@ int gm_launch_block_jacobi(gm_ctx* c, cudaStream_t s)
     const int nblk = (int)((c->N + 255) / 256);
     gm_block_jacobi_kernel<<<nblk, 256, 0, s>>>(a);
     GM_LAUNCHED(c);
+    if (c->g.kf >= 0 && c->pair_prec) {
+        gm_pair_block_kernel<<<(int)((c->g.nb + 127) / 128), 128, 0, s>>>(a, c->dKpair64.as<double>(),
+                                                                           c->dKpair32.as<float>());
+        GM_LAUNCHED(c);
+    }
     return GM_OK;
 }
 

@@ -875,6 +875,8 @@ int bind_impl(gm_ctx* c)
     const long long N3 = 3 * N;
     // optional tuning override of the bulk kernel's plane-chunk length
     if (const char* zc = std::getenv("GM_BULK_ZCHUNK")) c->zchunk_override = std::max(0, std::atoi(zc));
+    // K_T preconditioner: 6x6 lip-pair blocks (default) or 3x3 nodal blocks only (0)
+    if (const char* pp = std::getenv("GM_PAIR_PREC")) c->pair_prec = std::atoi(pp) != 0;
     // reduction partials: the fixed-grid reductions use 2 * GM_RED_BLOCKS slots,
     // a fused PCG step one per bulk CTA plus one per fault block
     const int gxp = (c->nx + 1 + 14) / 15, gyp = (c->ny + 1 + 14) / 15;
@@ -899,6 +901,7 @@ int bind_impl(gm_ctx* c)
         {&c->dinsitu, (size_t)3 * P * 8},
         {&c->ddiagK, (size_t)N3 * 8}, {&c->ddiagA, (size_t)N * 8},
         {&c->dKinv64, (size_t)12 * N * 8}, {&c->dKinv32, (size_t)6 * N * 4},
+        {&c->dKpair64, (size_t)36 * std::max<long long>(P, 1) * 8}, {&c->dKpair32, (size_t)36 * std::max<long long>(P, 1) * 4},
         {&c->dAinv64, (size_t)N * 8}, {&c->dAinv32, (size_t)N * 4},
         {&c->dFS64, (size_t)nel * 8}, {&c->dFS32, (size_t)nel * 4},
         {&c->dAfsinv64, (size_t)N * 8}, {&c->dAfsinv32, (size_t)N * 4},

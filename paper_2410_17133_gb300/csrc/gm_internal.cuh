@@ -268,6 +268,8 @@ struct gm_ctx {
     double adj_prtol = 1e-8;     // preconditioner tolerance
     int adj_schur = 0;           // preconditioner's Schur preconditioner
     DevBuf ddiagK, ddiagA, dKinv64, dKinv32, dAinv64, dAinv32;
+    DevBuf dKpair64, dKpair32;                         // 6x6 inverse blocks of the lip pairs (36 per pair)
+    bool pair_prec = true;                             // K_T preconditioner: lip pairs as 6x6 blocks
     DevBuf dFS64, dFS32, dAfsinv64, dAfsinv32;         // fixed-stress storage term
     DevBuf dscal;                                      // PcgScalars[4] + misc
     DevBuf dpart;                                      // reduction partials

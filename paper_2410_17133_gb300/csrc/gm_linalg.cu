@@ -121,15 +121,75 @@ struct RedCtx {
     unsigned* counter;
 };
 
+// K_T preconditioner blocks of the fault pairs: the thread of a lower-lip node
+// applies the 6x6 inverse to both lips of its pair (and updates both), the
+// thread of an upper-lip node skips it, so no two threads touch one node.
+template <typename T>
+struct PairPrec {
+    const T* inv;     // 36 per pair, field-major, row-major 6x6 (lower lip 0-2, upper 3-5); null: off
+    long long nb;     // pairs (= nodes per plane)
+    long long lo;     // first lower-lip node
+};
+
+template <typename T>
+__device__ inline void gm_pair_apply(const PairPrec<T>& pp, long long d, const T (&r6)[6], T (&z6)[6])
+{
+    // rows one at a time: the pair path is taken by one thread per fault pair
+    // and must not raise the register budget of the node path
+#pragma unroll 1
+    for (int a = 0; a < 6; ++a) {
+        T acc = T(0);
+#pragma unroll
+        for (int b = 0; b < 6; ++b) acc = fma(pp.inv[(a * 6 + b) * pp.nb + d], r6[b], acc);
+        z6[a] = acc;
+    }
+}
+
+template <typename T>
+__device__ inline void gm_dot_pair(const T (&r6)[6], const T (&z6)[6], double (&v)[2])
+{
+    const T r0[3] = {r6[0], r6[1], r6[2]}, r1[3] = {r6[3], r6[4], r6[5]};
+    const T z0[3] = {z6[0], z6[1], z6[2]}, z1[3] = {z6[3], z6[4], z6[5]};
+    gm_dot_node<T, 3>(r0, z0, v);
+    gm_dot_node<T, 3>(r1, z1, v);
+}
+
 template <typename T, int WHICH>
 __global__ void __launch_bounds__(256)
 gm_pcg_init_kernel(long long N, const T* b, const T* q, T* r, T* z, T* p, const T* mi, double rtol,
-                   PcgScalars* sc, RedCtx rc)
+                   PcgScalars* sc, RedCtx rc, PairPrec<T> pp)
 {
     constexpr int NC = Prec<T, WHICH>::NC;
     double v[2] = {0.0, 0.0};
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
+        if constexpr (WHICH == 0) {
+            const long long d = n - pp.lo;
+            if (pp.inv != nullptr && d >= 0 && d < 2 * pp.nb) {
+                if (d >= pp.nb) continue;              // upper lip: done with its pair
+                const long long nd[2] = {n, n + pp.nb};
+                T r6[6], z6[6];
+#pragma unroll
+                for (int s = 0; s < 2; ++s)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const long long k = c * N + nd[s];
+                        r6[3 * s + c] = q ? b[k] - q[k] : b[k];
+                    }
+                gm_pair_apply(pp, d, r6, z6);
+#pragma unroll
+                for (int s = 0; s < 2; ++s)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const long long k = c * N + nd[s];
+                        r[k] = r6[3 * s + c];
+                        z[k] = z6[3 * s + c];
+                        p[k] = T(0);
+                    }
+                gm_dot_pair(r6, z6, v);
+                continue;
+            }
+        }
         T rr[NC], zz[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) rr[c] = q ? b[c * N + n] - q[c * N + n] : b[c * N + n];
@@ -158,7 +218,7 @@ gm_pcg_init_kernel(long long N, const T* b, const T* q, T* r, T* z, T* p, const 
 template <typename T, int WHICH>
 __global__ void __launch_bounds__(256)
 gm_pcg_update_kernel(long long N, T* x, T* r, T* z, const T* p, const T* q, const T* mi,
-                     PcgScalars* sc, int maxit, RedCtx rc)
+                     PcgScalars* sc, int maxit, RedCtx rc, PairPrec<T> pp)
 {
     constexpr int NC = Prec<T, WHICH>::NC;
     if (sc->done) return;
@@ -166,6 +226,30 @@ gm_pcg_update_kernel(long long N, T* x, T* r, T* z, const T* p, const T* q, cons
     double v[2] = {0.0, 0.0};
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
+        if constexpr (WHICH == 0) {
+            const long long d = n - pp.lo;
+            if (pp.inv != nullptr && d >= 0 && d < 2 * pp.nb) {
+                if (d >= pp.nb) continue;              // upper lip: done with its pair
+                const long long nd[2] = {n, n + pp.nb};
+                T r6[6], z6[6];
+#pragma unroll
+                for (int s = 0; s < 2; ++s)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const long long k = c * N + nd[s];
+                        x[k] = fma(alpha, p[k], x[k]);
+                        r6[3 * s + c] = fma(-alpha, q[k], r[k]);
+                        r[k] = r6[3 * s + c];
+                    }
+                gm_pair_apply(pp, d, r6, z6);
+#pragma unroll
+                for (int s = 0; s < 2; ++s)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) z[c * N + nd[s]] = z6[3 * s + c];
+                gm_dot_pair(r6, z6, v);
+                continue;
+            }
+        }
         T rr[NC], zz[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
@@ -202,6 +286,18 @@ static RedCtx redctx(gm_ctx* c)
     return RedCtx{c->dpart.as<double>(), c->dcount.as<unsigned>()};
 }
 
+template <typename T>
+static PairPrec<T> pairprec(gm_ctx* c, int which)
+{
+    PairPrec<T> pp{nullptr, c->g.nb, -1};
+    if (which == 0 && c->g.kf >= 0 && c->pair_prec) {
+        if constexpr (sizeof(T) == 8) pp.inv = c->dKpair64.as<T>();
+        else pp.inv = c->dKpair32.as<T>();
+        pp.lo = (long long)c->g.kf * c->g.nb;
+    }
+    return pp;
+}
+
 // which 0: K_T block-Jacobi; 1: A22 Jacobi; 2: Jacobi of A22 plus the fixed-stress term
 template <typename T>
 static const T* prec_ptr(gm_ctx* c, int which)
@@ -221,20 +317,20 @@ int gm_launch_pcg_init(gm_ctx* c, int which, int prec, const void* b, const void
         if (which == 0)
             gm_pcg_init_kernel<double, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
                 N, (const double*)b, (const double*)q, (double*)r, (double*)z, (double*)p,
-                prec_ptr<double>(c, 0), rtol, sc, rc);
+                prec_ptr<double>(c, 0), rtol, sc, rc, pairprec<double>(c, 0));
         else
             gm_pcg_init_kernel<double, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
                 N, (const double*)b, (const double*)q, (double*)r, (double*)z, (double*)p,
-                prec_ptr<double>(c, which), rtol, sc, rc);
+                prec_ptr<double>(c, which), rtol, sc, rc, pairprec<double>(c, which));
     } else {
         if (which == 0)
             gm_pcg_init_kernel<float, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
                 N, (const float*)b, (const float*)q, (float*)r, (float*)z, (float*)p,
-                prec_ptr<float>(c, 0), rtol, sc, rc);
+                prec_ptr<float>(c, 0), rtol, sc, rc, pairprec<float>(c, 0));
         else
             gm_pcg_init_kernel<float, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
                 N, (const float*)b, (const float*)q, (float*)r, (float*)z, (float*)p,
-                prec_ptr<float>(c, which), rtol, sc, rc);
+                prec_ptr<float>(c, which), rtol, sc, rc, pairprec<float>(c, which));
     }
     GM_LAUNCHED(c);
     return GM_OK;
@@ -249,20 +345,20 @@ int gm_launch_pcg_update(gm_ctx* c, int which, int prec, void* x, void* r, void*
         if (which == 0)
             gm_pcg_update_kernel<double, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
                 N, (double*)x, (double*)r, (double*)z, (const double*)p, (const double*)q,
-                prec_ptr<double>(c, 0), sc, maxit, rc);
+                prec_ptr<double>(c, 0), sc, maxit, rc, pairprec<double>(c, 0));
         else
             gm_pcg_update_kernel<double, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
                 N, (double*)x, (double*)r, (double*)z, (const double*)p, (const double*)q,
-                prec_ptr<double>(c, which), sc, maxit, rc);
+                prec_ptr<double>(c, which), sc, maxit, rc, pairprec<double>(c, which));
     } else {
         if (which == 0)
             gm_pcg_update_kernel<float, 0><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
                 N, (float*)x, (float*)r, (float*)z, (const float*)p, (const float*)q,
-                prec_ptr<float>(c, 0), sc, maxit, rc);
+                prec_ptr<float>(c, 0), sc, maxit, rc, pairprec<float>(c, 0));
         else
             gm_pcg_update_kernel<float, 1><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
                 N, (float*)x, (float*)r, (float*)z, (const float*)p, (const float*)q,
-                prec_ptr<float>(c, which), sc, maxit, rc);
+                prec_ptr<float>(c, which), sc, maxit, rc, pairprec<float>(c, which));
     }
     GM_LAUNCHED(c);
     return GM_OK;
