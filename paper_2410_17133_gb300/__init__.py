@@ -91,6 +91,7 @@ _SIG = {
                                   C.POINTER(SolveReport), _P]),
     "gm_set_adjoint_options": (C.c_int, [_P, C.c_int, C.c_double, C.c_int]),
     "gm_set_insitu": (C.c_int, [_P, _P, _P, C.c_int64]),
+    "gm_set_preconditioner": (C.c_int, [_P, C.c_int]),
     "gm_adjoint_sweep_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _D,
                                         C.c_double, C.c_int, C.POINTER(SolveReport), _P]),
 }
@@ -174,6 +175,11 @@ class Solver:
     def fault(self, kf, kn, ks, f, w0, wk_par, k_perp, MF, tn0, tau0):
         fp = FaultParams(kn, ks, f, w0, wk_par, k_perp, MF, tn0, (C.c_double * 2)(*tau0))
         self._chk(self._L.gm_fault_plane(self.h, int(kf), C.byref(fp)))
+
+    def set_preconditioner(self, kind):
+        """gm_set_preconditioner: 0 block Jacobi (nodal and lip-pair blocks),
+        1 multigrid V-cycle for the FP32 K_T inner solves."""
+        self._chk(self._L.gm_set_preconditioner(self.h, int(kind)))
 
     def set_insitu(self, tn0=None, tau0=None):
         """gm_set_insitu: per-pair in-situ tractions, tn0 (P,) and tau0 (P, 2) in

@@ -13,7 +13,7 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libgm.so")
 SOURCES = ["gm_apply_f64.cu", "gm_apply_f32.cu", "gm_fault.cu", "gm_linalg.cu", "gm_solve.cu",
-           "gm_host.cu", "gm_noalloc.cu", "gm_adjoint.cu"]
+           "gm_host.cu", "gm_noalloc.cu", "gm_adjoint.cu", "gm_mg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -260,6 +260,7 @@ int gm_destroy(gm_ctx* c)
     if (!c) return GM_OK;
     cudaSetDevice(c->device);
     c->drop_graphs();
+    gm_mg_release(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->hpin) cudaFreeHost(c->hpin);
     delete c;
@@ -316,6 +317,15 @@ static int gm_insitu_floor(gm_ctx* c)
             }
         }
     }
+    return GM_OK;
+}
+
+int gm_set_preconditioner(gm_ctx* c, int kind)
+{
+    if (!c) return GM_EINVAL;
+    if (kind != 0 && kind != 1) return c->set_err(GM_EINVAL, "set_preconditioner: kind must be 0 or 1");
+    if (kind != c->precond) c->drop_graphs();
+    c->precond = kind;
     return GM_OK;
 }
 
@@ -786,6 +796,7 @@ int bind_impl(gm_ctx* c)
 {
     (void)cudaGetLastError();   // start from a clean runtime error state
     c->drop_graphs();           // graphs hold pointers into the buffers freed below
+    gm_mg_release(c);           // coarse levels are rebuilt from the new set-up on first use
     if (!c->has_mesh || !c->has_mat) return c->set_err(GM_ESTATE, "bind: mesh and materials required");
     const long long N = n_nodes_of(c);
     const long long nel = (long long)c->nx * c->ny * c->nz;

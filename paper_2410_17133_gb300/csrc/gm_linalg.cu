@@ -9,6 +9,7 @@
 // returns at once when `done` is set, so the host only checks now and then.
 // Vectors may be FP32 (mixed precision) or FP64; dots always accumulate in FP64.
 #include "gm_internal.cuh"
+#include "gm_pcgvec.cuh"
 
 template <int NV>
 __device__ void gm_block_sum_l(double (&v)[NV], double* sh)
@@ -66,93 +67,10 @@ __device__ bool gm_grid_sum_l(double (&v)[NV], double* part, unsigned* counter)
     return threadIdx.x == 0;
 }
 
-// Preconditioner application for one node, in the vector precision T.
-// WHICH 0: 3 components, 3x3 symmetric block inverse (6 per node);
-// WHICH 1: 1 component, diagonal inverse.
-template <typename T, int WHICH>
-struct Prec;
-template <typename T>
-struct Prec<T, 0> {
-    static constexpr int NC = 3;
-    __device__ static void apply(const T* mi, long long N, long long n, const T (&r)[3], T (&z)[3]) {
-        const T i0 = mi[n], i1 = mi[N + n], i2 = mi[2 * N + n];
-        const T i3 = mi[3 * N + n], i4 = mi[4 * N + n], i5 = mi[5 * N + n];
-        z[0] = i0 * r[0] + i1 * r[1] + i2 * r[2];
-        z[1] = i1 * r[0] + i3 * r[1] + i4 * r[2];
-        z[2] = i2 * r[0] + i4 * r[1] + i5 * r[2];
-    }
-};
-template <typename T>
-struct Prec<T, 1> {
-    static constexpr int NC = 1;
-    __device__ static void apply(const T* mi, long long, long long n, const T (&r)[1], T (&z)[1]) {
-        z[0] = mi[n] * r[0];
-    }
-};
-
-// Add r.z and r.r of one node to the FP64 accumulators v.  Displacement
-// vectors (3 components, force-scale residuals) sum the node's components in
-// the vector precision first; pressure vectors (flow residuals of order
-// 1e-15..1e-20 m^3, whose squares would underflow in FP32) multiply in FP64,
-// where the product of two floats is exact.
-template <typename T, int NC>
-__device__ inline void gm_dot_node(const T (&r)[NC], const T (&z)[NC], double (&v)[2])
-{
-    if constexpr (NC == 3) {
-        T a = T(0), b = T(0);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            a = fma(r[c], z[c], a);
-            b = fma(r[c], r[c], b);
-        }
-        v[0] += (double)a;
-        v[1] += (double)b;
-    } else {
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            v[0] += (double)r[c] * (double)z[c];
-            v[1] += (double)r[c] * (double)r[c];
-        }
-    }
-}
-
 struct RedCtx {
     double* part;
     unsigned* counter;
 };
-
-// K_T preconditioner blocks of the fault pairs: the thread of a lower-lip node
-// applies the 6x6 inverse to both lips of its pair (and updates both), the
-// thread of an upper-lip node skips it, so no two threads touch one node.
-template <typename T>
-struct PairPrec {
-    const T* inv;     // 36 per pair, field-major, row-major 6x6 (lower lip 0-2, upper 3-5); null: off
-    long long nb;     // pairs (= nodes per plane)
-    long long lo;     // first lower-lip node
-};
-
-template <typename T>
-__device__ inline void gm_pair_apply(const PairPrec<T>& pp, long long d, const T (&r6)[6], T (&z6)[6])
-{
-    // rows one at a time: the pair path is taken by one thread per fault pair
-    // and must not raise the register budget of the node path
-#pragma unroll 1
-    for (int a = 0; a < 6; ++a) {
-        T acc = T(0);
-#pragma unroll
-        for (int b = 0; b < 6; ++b) acc = fma(pp.inv[(a * 6 + b) * pp.nb + d], r6[b], acc);
-        z6[a] = acc;
-    }
-}
-
-template <typename T>
-__device__ inline void gm_dot_pair(const T (&r6)[6], const T (&z6)[6], double (&v)[2])
-{
-    const T r0[3] = {r6[0], r6[1], r6[2]}, r1[3] = {r6[3], r6[4], r6[5]};
-    const T z0[3] = {z6[0], z6[1], z6[2]}, z1[3] = {z6[3], z6[4], z6[5]};
-    gm_dot_node<T, 3>(r0, z0, v);
-    gm_dot_node<T, 3>(r1, z1, v);
-}
 
 template <typename T, int WHICH>
 __global__ void __launch_bounds__(256)
@@ -505,6 +423,75 @@ int gm_launch_jacobi_apply(gm_ctx* c, int which, const double* r, double* z, cud
         gm_jacobi_apply_kernel<0><<<GM_RED_BLOCKS, 256, 0, s>>>(c->N, c->dKinv64.as<double>(), r, z);
     else
         gm_jacobi_apply_kernel<1><<<GM_RED_BLOCKS, 256, 0, s>>>(c->N, c->dAinv64.as<double>(), r, z);
+    GM_LAUNCHED(c);
+    return GM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// PCG steps around the multigrid preconditioner (FP32 K_T solves): the update
+// pass leaves z to the V-cycle, and a second pass forms r.z and beta.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+gm_pcg_update_noz_kernel(long long n, float* x, float* r, const float* p, const float* q, PcgScalars* sc,
+                         int maxit, RedCtx rc)
+{
+    if (sc->done) return;
+    const float alpha = (float)sc->alpha;
+    double v[1] = {0.0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        x[i] = fmaf(alpha, p[i], x[i]);
+        const float ri = fmaf(-alpha, q[i], r[i]);
+        r[i] = ri;
+        v[0] += (double)ri * (double)ri;
+    }
+    if (gm_grid_sum_l<1>(v, rc.part, rc.counter)) {
+        sc->it += 1;
+        sc->rr = v[0];
+        if (!isfinite(v[0])) {
+            sc->status = GM_ENAN;
+            sc->done = 1;
+        } else if (v[0] <= sc->tol2) {
+            sc->done = 1;
+        } else if (sc->it >= maxit) {
+            sc->status = GM_ENOCONV;
+            sc->done = 1;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+gm_pcg_rz_kernel(long long n, const float* r, const float* z, PcgScalars* sc, int init, RedCtx rc)
+{
+    if (sc->done) return;
+    double v[1] = {0.0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        v[0] += (double)r[i] * (double)z[i];
+    if (gm_grid_sum_l<1>(v, rc.part, rc.counter)) {
+        if (!isfinite(v[0]) || !(v[0] > 0.0)) {
+            sc->status = isfinite(v[0]) ? GM_ENOCONV : GM_ENAN;
+            sc->done = 1;
+        } else if (init) {
+            sc->rz = v[0];
+        } else {
+            sc->beta = v[0] / sc->rz;
+            sc->rz = v[0];
+        }
+    }
+}
+
+int gm_launch_pcg_update_noz(gm_ctx* c, float* x, float* r, const float* p, const float* q, PcgScalars* sc,
+                             int maxit, cudaStream_t s)
+{
+    gm_pcg_update_noz_kernel<<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(3 * c->N, x, r, p, q, sc, maxit, redctx(c));
+    GM_LAUNCHED(c);
+    return GM_OK;
+}
+
+int gm_launch_pcg_rz(gm_ctx* c, const float* r, const float* z, PcgScalars* sc, int init, cudaStream_t s)
+{
+    gm_pcg_rz_kernel<<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(3 * c->N, r, z, sc, init, redctx(c));
     GM_LAUNCHED(c);
     return GM_OK;
 }

@@ -1,0 +1,516 @@
+// Geometric multigrid preconditioner for the FP32 K_T inner solves.
+//
+// The inner solves of the partitioned scheme (Sec. 3.3.2) on K_T take
+// thousands of block-Jacobi PCG iterations on the larger grids (their count
+// grows with the grid size), so the FP32 K_T solves may use one V-cycle as the
+// preconditioner instead.  The structured grid is halved in every direction
+// within each of the two fault blocks (the fault node plane kf and the block
+// boundaries stay node planes), down to a few cells:
+//   - coarse operators are rediscretised: each coarse level is a child
+//     context with E averaged over the 8 fine elements of a coarse element,
+//     the Dirichlet bits and the fault tangent D of the coincident fine node
+//     or pair, and the reference cell of twice the spacing;
+//   - prolongation is trilinear interpolation inside each block, restriction
+//     its transpose (full weighting), so the cycle never couples the lips;
+//   - smoothing is a degree-2 Chebyshev polynomial in M^-1 K_T with M the
+//     nodal / lip-pair block Jacobi, over [0.25, 1.15] x the largest
+//     eigenvalue (power iteration at set-up); the coarsest level runs a
+//     degree-16 polynomial over [0.01, 1.15] x that eigenvalue.
+// Pre- and post-smoothing use the same polynomial, so the cycle is a
+// symmetric positive definite operator and plain PCG stays valid.
+// Everything is enqueued on the caller's stream without host synchronisation
+// (except the one-time set-up), so the PCG iterations remain graph-capturable.
+#include <cmath>
+
+#include "gm_internal.cuh"
+#include "gm_pcgvec.cuh"
+
+namespace {
+
+constexpr int MG_MIN_CELLS = 2;     // coarse grids keep at least this many cells per direction
+constexpr int MG_MAX_LEVELS = 8;
+constexpr int MG_SMOOTH_DEG = 2;
+constexpr int MG_COARSE_DEG = 16;
+
+__device__ inline void mg_plane(const GridDesc& g, int kk, int* o, int* up)
+{
+    if (g.kf < 0) { *o = kk; *up = 0; return; }
+    *up = kk > g.kf ? 1 : 0;
+    *o = *up ? kk - 1 : kk;
+}
+__device__ inline int mg_ext(const GridDesc& g, int o, int up) { return (g.kf >= 0 && up) ? o + 1 : o; }
+
+// b_c = R (b_f - y_f): full weighting inside each block; constrained coarse
+// components 0.  y_f may be null (then r_f = b_f).
+__global__ void mg_restrict_kernel(GridDesc F, GridDesc Cg, const float* bf, const float* yf, float* bc,
+                                   const uint8_t* maskc, const int* skip)
+{
+    if (skip && *skip) return;
+    const long long nc = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (nc >= Cg.N) return;
+    const int ic = (int)(nc % (Cg.nx + 1));
+    const long long t = nc / (Cg.nx + 1);
+    const int jc = (int)(t % (Cg.ny + 1)), kkc = (int)(t / (Cg.ny + 1));
+    int oc, up;
+    mg_plane(Cg, kkc, &oc, &up);
+    const int olo = (F.kf >= 0 && up) ? F.kf : 0;
+    const int ohi = (F.kf >= 0 && !up) ? F.kf : F.nz;
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int dk = -1; dk <= 1; ++dk) {
+        const int o = 2 * oc + dk;
+        if (o < olo || o > ohi) continue;
+        const float wz = dk ? 0.5f : 1.f;
+        const long long kk = mg_ext(F, o, up);
+        for (int dj = -1; dj <= 1; ++dj) {
+            const int j = 2 * jc + dj;
+            if (j < 0 || j > F.ny) continue;
+            const float wy = dj ? 0.5f : 1.f;
+            for (int di = -1; di <= 1; ++di) {
+                const int i = 2 * ic + di;
+                if (i < 0 || i > F.nx) continue;
+                const float w = wz * wy * (di ? 0.5f : 1.f);
+                const long long f = i + (long long)(F.nx + 1) * (j + (long long)(F.ny + 1) * kk);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float r = bf[c * F.N + f] - (yf ? yf[c * F.N + f] : 0.f);
+                    acc[c] = fmaf(w, r, acc[c]);
+                }
+            }
+        }
+    }
+    const unsigned m = maskc[nc];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) bc[c * Cg.N + nc] = ((m >> c) & 1u) ? 0.f : acc[c];
+}
+
+// x_f += P x_c: trilinear interpolation inside each block; constrained fine
+// components unchanged.
+__global__ void mg_prolong_kernel(GridDesc F, GridDesc Cg, const float* xc, float* xf, const uint8_t* maskf,
+                                  const int* skip)
+{
+    if (skip && *skip) return;
+    const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F.N) return;
+    const int i = (int)(f % (F.nx + 1));
+    const long long t = f / (F.nx + 1);
+    const int j = (int)(t % (F.ny + 1)), kk = (int)(t / (F.ny + 1));
+    int o, up;
+    mg_plane(F, kk, &o, &up);
+    int pi[2], pj[2], po[2];
+    float wi[2], wj[2], wo[2];
+    const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, no = (o & 1) ? 2 : 1;
+    pi[0] = i >> 1; pi[1] = (i + 1) >> 1; wi[0] = wi[1] = (i & 1) ? 0.5f : 1.f;
+    pj[0] = j >> 1; pj[1] = (j + 1) >> 1; wj[0] = wj[1] = (j & 1) ? 0.5f : 1.f;
+    po[0] = o >> 1; po[1] = (o + 1) >> 1; wo[0] = wo[1] = (o & 1) ? 0.5f : 1.f;
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < no; ++a) {
+        const long long kkc = mg_ext(Cg, po[a], up);
+        for (int b = 0; b < nj; ++b)
+            for (int e = 0; e < ni; ++e) {
+                const float w = wo[a] * wj[b] * wi[e];
+                const long long nc = pi[e] + (long long)(Cg.nx + 1) * (pj[b] + (long long)(Cg.ny + 1) * kkc);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc[c] = fmaf(w, xc[c * Cg.N + nc], acc[c]);
+            }
+    }
+    const unsigned m = maskf[f];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        if (!((m >> c) & 1u)) xf[c * F.N + f] += acc[c];
+}
+
+// Fault tangent of the coarse pairs: that of the coincident fine pair.
+__global__ void mg_inject_d_kernel(GridDesc F, GridDesc Cg, const double* d64f, double* d64c, float* d32c)
+{
+    const long long qc = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (qc >= Cg.nb) return;
+    const int ic = (int)(qc % (Cg.nx + 1)), jc = (int)(qc / (Cg.nx + 1));
+    const long long qf = 2LL * ic + (long long)(F.nx + 1) * (2LL * jc);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const double v = d64f[q * F.nb + qf];
+        d64c[q * Cg.nb + qc] = v;
+        d32c[q * Cg.nb + qc] = (float)v;
+    }
+}
+
+// One Chebyshev step: r = b - y (y null: x = 0, r = b), z = M^-1 r,
+// d = c1 d + c2 z (c1 = 0: d = c2 z), x = x + d (xzero: x = d).
+__global__ void __launch_bounds__(256) mg_cheb_kernel(long long N, const float* b, const float* y, float* x,
+                                                      float* d, const float* mi, PairPrec<float> pp,
+                                                      const double* coef, int xzero, const int* skip)
+{
+    if (skip && *skip) return;
+    const float c1 = (float)coef[0], c2 = (float)coef[1];
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const long long dd = n - pp.lo;
+        if (pp.inv != nullptr && dd >= 0 && dd < 2 * pp.nb) {
+            if (dd >= pp.nb) continue;                 // upper lip: done with its pair
+            const long long nd[2] = {n, n + pp.nb};
+            float r6[6], z6[6];
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const long long k = c * N + nd[s];
+                    r6[3 * s + c] = b[k] - (y ? y[k] : 0.f);
+                }
+            gm_pair_apply(pp, dd, r6, z6);
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const long long k = c * N + nd[s];
+                    const float dn = c1 == 0.f ? c2 * z6[3 * s + c] : fmaf(c1, d[k], c2 * z6[3 * s + c]);
+                    d[k] = dn;
+                    x[k] = xzero ? dn : x[k] + dn;
+                }
+            continue;
+        }
+        float r[3], z[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r[c] = b[c * N + n] - (y ? y[c * N + n] : 0.f);
+        Prec<float, 0>::apply(mi, N, n, r, z);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long k = c * N + n;
+            const float dn = c1 == 0.f ? c2 * z[c] : fmaf(c1, d[k], c2 * z[c]);
+            d[k] = dn;
+            x[k] = xzero ? dn : x[k] + dn;
+        }
+    }
+}
+
+// Per-block partial sums of v.v (set-up only; summed on the host in block order).
+__global__ void __launch_bounds__(256) mg_norm2_kernel(long long n, const float* v, double* part)
+{
+    __shared__ double sh[8];
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        acc += (double)v[i] * (double)v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += sh[w];
+        part[blockIdx.x] = s;
+    }
+}
+
+__global__ void mg_scale_kernel(long long n, float* v, float a)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        v[i] *= a;
+}
+
+// Deterministic start vector of the power iteration (free components only).
+__global__ void mg_seed_kernel(long long N, const uint8_t* mask, float* v)
+{
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const unsigned m = mask[n];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            unsigned h = (unsigned)(n * 3 + c) * 2654435761u;
+            h ^= h >> 15;
+            h *= 2246822519u;
+            h ^= h >> 13;
+            v[c * N + n] = ((m >> c) & 1u) ? 0.f : ((float)(h & 0xffffu) / 32768.f - 1.f);
+        }
+    }
+}
+
+PairPrec<float> level_pairs(gm_ctx* x)
+{
+    PairPrec<float> pp{nullptr, x->g.nb, -1};
+    if (x->g.kf >= 0 && x->pair_prec) {
+        pp.inv = x->dKpair32.as<float>();
+        pp.lo = (long long)x->g.kf * x->g.nb;
+    }
+    return pp;
+}
+
+bool coarsenable(const gm_ctx* x)
+{
+    if (x->nx % 2 || x->ny % 2 || x->nz % 2) return false;
+    if (x->nx / 2 < MG_MIN_CELLS || x->ny / 2 < MG_MIN_CELLS || x->nz / 2 < MG_MIN_CELLS) return false;
+    if (x->has_fault) {
+        if (x->kf_orig % 2) return false;
+        if (x->kf_orig / 2 < 1 || (x->nz - x->kf_orig) / 2 < 1) return false;
+    }
+    return true;
+}
+
+// Child context one level coarser than x (E, k averaged over the 8 fine
+// elements; Dirichlet bits of the coincident fine node).
+int make_child(gm_ctx* x, gm_ctx** out)
+{
+    gm_ctx* ch = nullptr;
+    int rc = gm_create(&ch, x->device);
+    if (rc) return x->set_err(rc, "multigrid: cannot create a coarse level");
+    const int nxc = x->nx / 2, nyc = x->ny / 2, nzc = x->nz / 2;
+    const double hc[3] = {2 * x->h[0], 2 * x->h[1], 2 * x->h[2]};
+    auto fail = [&](const char* what) {
+        const std::string m = std::string("multigrid: ") + what + ": " + gm_last_error(ch);
+        gm_destroy(ch);
+        return x->set_err(GM_EINVAL, m);
+    };
+    if (gm_mesh_structured(ch, nxc, nyc, nzc, x->origin, hc, x->shear)) return fail("mesh");
+    if (x->has_fault && gm_fault_plane(ch, x->kf_orig / 2, &x->fp)) return fail("fault");
+    const long long nelc = (long long)nxc * nyc * nzc;
+    std::vector<double> Ec(nelc, 0.0), kc(nelc, 0.0);
+    for (int ek = 0; ek < nzc; ++ek)
+        for (int ej = 0; ej < nyc; ++ej)
+            for (int ei = 0; ei < nxc; ++ei) {
+                const long long e = ei + (long long)nxc * (ej + (long long)nyc * ek);
+                for (int a = 0; a < 8; ++a) {
+                    const long long ef = (2 * ei + (a & 1)) + (long long)x->nx *
+                                         ((2 * ej + ((a >> 1) & 1)) + (long long)x->ny * (2 * ek + (a >> 2)));
+                    Ec[e] += 0.125 * x->E[ef];
+                    kc[e] += 0.125 * x->kperm[ef];
+                }
+            }
+    if (gm_set_materials(ch, Ec.data(), kc.data(), nelc, x->nu, x->alpha, x->M, x->mu_f)) return fail("materials");
+    const long long npc = nzc + 1 + (x->has_fault ? 1 : 0);
+    const long long nbc = (long long)(nxc + 1) * (nyc + 1), Nc = nbc * npc;
+    const long long Nf = x->N;
+    const int kff = x->has_fault ? x->kf_orig : -1, kfc = x->has_fault ? x->kf_orig / 2 : -1;
+    std::vector<uint8_t> fixc(4 * Nc, 0);
+    for (long long kkc = 0; kkc < npc; ++kkc) {
+        const bool up = kfc >= 0 && kkc > kfc;
+        const long long oc = up ? kkc - 1 : kkc;
+        const long long kkf = (kff >= 0 && up) ? 2 * oc + 1 : 2 * oc;
+        for (int jc = 0; jc <= nyc; ++jc)
+            for (int ic = 0; ic <= nxc; ++ic) {
+                const long long nc = ic + (long long)(nxc + 1) * (jc + (long long)(nyc + 1) * kkc);
+                const long long nf = 2LL * ic + (long long)(x->nx + 1) * (2LL * jc + (long long)(x->ny + 1) * kkf);
+                for (int d = 0; d < 4; ++d) fixc[d * Nc + nc] = x->fixed[d * Nf + nf];
+            }
+    }
+    if (gm_set_dirichlet(ch, fixc.data(), 4 * Nc)) return fail("dirichlet");
+    ch->pair_prec = x->pair_prec;
+    if (gm_assemble_or_bind(ch)) return fail("bind");
+    *out = ch;
+    return GM_OK;
+}
+
+int apply_kt(gm_ctx* x, const float* v, float* y, const int* skip, cudaStream_t s)
+{
+    return gm_launch_apply_f32(x, GM_MODE_KT, 1.0, 0.0, 0.0, 0.0, 0.0, v, nullptr, y, nullptr, s, skip);
+}
+
+int cheb_step(gm_ctx* c, const MGLevel& L, int k, bool xzero, const int* skip, cudaStream_t s)
+{
+    gm_ctx* x = L.cx;
+    const double* cf = c->mg_coef.as<double>() + 2 * (L.coef_off + k);
+    mg_cheb_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(x->N, L.b, xzero ? nullptr : L.y, L.x, L.d,
+                                                 x->dKinv32.as<float>(), level_pairs(x), cf, xzero ? 1 : 0, skip);
+    GM_LAUNCHED(c);
+    return GM_OK;
+}
+
+// deg Chebyshev steps on level L (from x = 0 if xzero)
+int smooth(gm_ctx* c, const MGLevel& L, int deg, bool xzero, const int* skip, cudaStream_t s)
+{
+    int rc;
+    for (int k = 0; k < deg; ++k) {
+        const bool z0 = xzero && k == 0;
+        if (!z0 && (rc = apply_kt(L.cx, L.x, L.y, skip, s))) return rc;
+        if ((rc = cheb_step(c, L, k, z0, skip, s))) return rc;
+    }
+    return GM_OK;
+}
+
+int vcycle(gm_ctx* c, size_t l, const int* skip, cudaStream_t s)
+{
+    const MGLevel& L = c->mg[l];
+    int rc;
+    if (l + 1 == c->mg.size()) return smooth(c, L, L.deg, true, skip, s);
+    if ((rc = smooth(c, L, L.deg, true, skip, s))) return rc;
+    if ((rc = apply_kt(L.cx, L.x, L.y, skip, s))) return rc;
+    const MGLevel& C = c->mg[l + 1];
+    mg_restrict_kernel<<<(int)((C.cx->N + 255) / 256), 256, 0, s>>>(L.cx->g, C.cx->g, L.b, L.y, C.b,
+                                                                     C.cx->dmask.as<uint8_t>(), skip);
+    GM_LAUNCHED(c);
+    if ((rc = vcycle(c, l + 1, skip, s))) return rc;
+    mg_prolong_kernel<<<(int)((L.cx->N + 255) / 256), 256, 0, s>>>(L.cx->g, C.cx->g, C.x, L.x,
+                                                                    L.cx->dmask.as<uint8_t>(), skip);
+    GM_LAUNCHED(c);
+    return smooth(c, L, L.deg, false, skip, s);
+}
+
+// Chebyshev coefficients (c1, c2) of step k over [lo, hi] (Saad, Iterative
+// Methods for Sparse Linear Systems, Alg. 12.1, written as updates of x).
+void cheb_coefs(double lo, double hi, int deg, std::vector<double>& out)
+{
+    const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    out.push_back(0.0);
+    out.push_back(1.0 / theta);
+    for (int k = 1; k < deg; ++k) {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        out.push_back(rn * rho);
+        out.push_back(2.0 * rn / delta);
+        rho = rn;
+    }
+}
+
+int norm2(gm_ctx* c, long long n, const float* v, double* out)
+{
+    double* part = c->dpart.as<double>();
+    mg_norm2_kernel<<<GM_RED_BLOCKS, 256>>>(n, v, part);
+    GM_LAUNCHED(c);
+    std::vector<double> h(GM_RED_BLOCKS);
+    GM_CUDA_TRY(c, cudaMemcpy(h.data(), part, GM_RED_BLOCKS * sizeof(double), cudaMemcpyDeviceToHost));
+    double t = 0.0;
+    for (double x : h) t += x;
+    *out = t;
+    return GM_OK;
+}
+
+// Largest eigenvalue of M^-1 K_T on level L by 12 power iterations.
+int estimate_lmax(gm_ctx* c, MGLevel& L)
+{
+    gm_ctx* x = L.cx;
+    const long long n3 = 3 * x->N;
+    float* v = L.b;     // scratch during set-up
+    mg_seed_kernel<<<GM_RED_BLOCKS, 256>>>(x->N, x->dmask.as<uint8_t>(), v);
+    GM_LAUNCHED(c);
+    double nv;
+    int rc;
+    if ((rc = norm2(c, n3, v, &nv))) return rc;
+    if (!(nv > 0)) { L.lmax = 1.0; return GM_OK; }
+    mg_scale_kernel<<<GM_RED_BLOCKS, 256>>>(n3, v, (float)(1.0 / std::sqrt(nv)));
+    GM_LAUNCHED(c);
+    const double* unit = c->mg_coef.as<double>();   // (0, 1): z = M^-1 b
+    double lam = 0.0;
+    for (int it = 0; it < 12; ++it) {
+        if ((rc = apply_kt(x, v, L.y, nullptr, 0))) return rc;
+        mg_cheb_kernel<<<GM_RED_BLOCKS, 256>>>(x->N, L.y, nullptr, L.x, L.d, x->dKinv32.as<float>(),
+                                               level_pairs(x), unit, 1, nullptr);
+        GM_LAUNCHED(c);
+        double nw;
+        if ((rc = norm2(c, n3, L.x, &nw))) return rc;
+        lam = std::sqrt(nw);
+        if (!(lam > 0) || !std::isfinite(lam)) return c->set_err(GM_ENAN, "multigrid: eigenvalue estimate failed");
+        GM_CUDA_TRY(c, cudaMemcpy(v, L.x, n3 * sizeof(float), cudaMemcpyDeviceToDevice));
+        mg_scale_kernel<<<GM_RED_BLOCKS, 256>>>(n3, v, (float)(1.0 / lam));
+        GM_LAUNCHED(c);
+    }
+    L.lmax = lam;
+    return GM_OK;
+}
+
+int inject_and_refresh(gm_ctx* c, cudaStream_t s)
+{
+    for (size_t l = 1; l < c->mg.size(); ++l) {
+        gm_ctx* f = c->mg[l - 1].cx;
+        gm_ctx* x = c->mg[l].cx;
+        if (x->g.kf >= 0) {
+            mg_inject_d_kernel<<<(int)((x->g.nb + 255) / 256), 256, 0, s>>>(f->g, x->g, f->dD64.as<double>(),
+                                                                           x->dD64.as<double>(), x->dD32.as<float>());
+            GM_LAUNCHED(c);
+        }
+        int rc = gm_launch_block_jacobi(x, s);
+        if (rc) return c->set_err(rc, std::string("multigrid: ") + gm_last_error(x));
+    }
+    return GM_OK;
+}
+
+int build(gm_ctx* c)
+{
+    c->mg.clear();
+    MGLevel L0;
+    L0.cx = c;
+    c->mg.push_back(L0);
+    gm_ctx* cur = c;
+    while (coarsenable(cur) && (int)c->mg.size() < MG_MAX_LEVELS) {
+        gm_ctx* ch = nullptr;
+        int rc = make_child(cur, &ch);
+        if (rc) { gm_mg_release(c); return rc; }
+        MGLevel L;
+        L.cx = ch;
+        L.b = ch->k_b32.as<float>();
+        L.x = ch->k_x32.as<float>();
+        L.d = ch->k_z32.as<float>();
+        L.y = ch->k_q32.as<float>();
+        c->mg.push_back(L);
+        cur = ch;
+    }
+    if (c->mg.size() < 2) {
+        c->mg.clear();
+        return c->set_err(GM_EINVAL, "multigrid: grid cannot be coarsened (even cell counts and fault index needed)");
+    }
+    const long long n3 = 3 * c->N;
+    GM_CUDA_TRY(c, c->mg_d0.alloc(n3 * sizeof(float)));
+    GM_CUDA_TRY(c, c->mg_y0.alloc(n3 * sizeof(float)));
+    c->mg[0].d = c->mg_d0.as<float>();
+    c->mg[0].y = c->mg_y0.as<float>();
+    // coefficient slot 0 = (0, 1) for the eigenvalue estimate; levels follow
+    std::vector<double> coef = {0.0, 1.0};
+    GM_CUDA_TRY(c, c->mg_coef.alloc(2 * sizeof(double) * (1 + MG_MAX_LEVELS * MG_COARSE_DEG)));
+    GM_CUDA_TRY(c, cudaMemcpy(c->mg_coef.p, coef.data(), 2 * sizeof(double), cudaMemcpyHostToDevice));
+    int rc;
+    if ((rc = inject_and_refresh(c, 0))) { gm_mg_release(c); return rc; }
+    // level 0 vectors during set-up: PCG scratch of the context
+    c->mg[0].b = c->k_b32.as<float>();
+    c->mg[0].x = c->k_x32.as<float>();
+    for (auto& L : c->mg)
+        if ((rc = estimate_lmax(c, L))) { gm_mg_release(c); return rc; }
+    c->mg[0].b = nullptr;
+    c->mg[0].x = nullptr;
+    int off = 1;
+    for (size_t l = 0; l < c->mg.size(); ++l) {
+        MGLevel& L = c->mg[l];
+        const bool last = l + 1 == c->mg.size();
+        L.deg = last ? MG_COARSE_DEG : MG_SMOOTH_DEG;
+        L.coef_off = off;
+        const double hi = 1.15 * L.lmax;
+        cheb_coefs(last ? 0.01 * hi : 0.25 * L.lmax, hi, L.deg, coef);
+        off += L.deg;
+    }
+    GM_CUDA_TRY(c, cudaMemcpy(c->mg_coef.p, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice));
+    GM_CUDA_TRY(c, cudaDeviceSynchronize());
+    return GM_OK;
+}
+
+}  // namespace
+
+void gm_mg_release(gm_ctx* c)
+{
+    for (size_t l = 1; l < c->mg.size(); ++l) gm_destroy(c->mg[l].cx);
+    c->mg.clear();
+    c->mg_d0.release();
+    c->mg_y0.release();
+    c->mg_coef.release();
+}
+
+int gm_mg_prepare(gm_ctx* c, cudaStream_t s)
+{
+    if (c->mg.empty()) {
+        // the one-time build runs on the default stream and reads the block
+        // Jacobi that the caller may still be computing on s
+        GM_CUDA_TRY(c, cudaStreamSynchronize(s));
+        return build(c);
+    }
+    return inject_and_refresh(c, s);
+}
+
+int gm_mg_vcycle(gm_ctx* c, const float* r, float* z, const int* skip, cudaStream_t s)
+{
+    if (c->mg.empty()) return c->set_err(GM_ESTATE, "multigrid: not prepared");
+    c->mg[0].b = const_cast<float*>(r);
+    c->mg[0].x = z;
+    long long before = 0;
+    for (size_t l = 1; l < c->mg.size(); ++l) before += c->mg[l].cx->launches;
+    const int rc = vcycle(c, 0, skip, s);
+    long long after = 0;
+    for (size_t l = 1; l < c->mg.size(); ++l) after += c->mg[l].cx->launches;
+    c->launches += after - before;   // the coarse levels' kernels count as this context's
+    return rc;
+}
