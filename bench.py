@@ -379,6 +379,8 @@ def run_gm(args, rank, world, local_rank):
             "config": dict(cfg, dofs=ndof, newton_rtol=NEWTON_RTOL,
                            steps_timed=f"{W}..{W + K - 1} of the schedule",
                            l2="flushed (512 MB write) between timed steps and between timed applies",
+                           inner_solvers="FP32 K_T: PCG with a multigrid V-cycle; A22: Jacobi PCG; "
+                                         "FP64 comparison: PCG with nodal/lip-pair block Jacobi",
                            parallelism=f"replicas{world}" if world > 1 else "single"),
             "roofline": roof, "apply": apply, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "gpu_launches": int(launches),
