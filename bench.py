@@ -253,7 +253,9 @@ def run_gm(args, rank, world, local_rank):
     with ClockSampler(local_rank) as clk:
         barrier()
         t_wall0 = time.perf_counter()
+        torch.cuda.nvtx.range_push("timed_steps")    # lets a profiler select these launches
         ms, reps = timed_steps(s, range(W, W + K), gm.F32)
+        torch.cuda.nvtx.range_pop()
         t_wall = time.perf_counter() - t_wall0
     clocks = clk.summary()
     l1, _ = s.counters()
