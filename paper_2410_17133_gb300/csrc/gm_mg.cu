@@ -15,22 +15,44 @@
 //   - smoothing is a degree-2 Chebyshev polynomial in M^-1 K_T with M the
 //     nodal / lip-pair block Jacobi, over [0.25, 1.15] x the largest
 //     eigenvalue (power iteration at set-up); the coarsest level runs a
-//     degree-16 polynomial over [0.01, 1.15] x that eigenvalue.
+//     degree-8 polynomial (by default) over [0.01, 1.15] x that eigenvalue.
 // Pre- and post-smoothing use the same polynomial, so the cycle is a
 // symmetric positive definite operator and plain PCG stays valid.
 // Everything is enqueued on the caller's stream without host synchronisation
 // (except the one-time set-up), so the PCG iterations remain graph-capturable.
 #include <cmath>
+#include <cstdlib>
 
 #include "gm_internal.cuh"
 #include "gm_pcgvec.cuh"
 
 namespace {
 
-constexpr int MG_MIN_CELLS = 2;     // coarse grids keep at least this many cells per direction
 constexpr int MG_MAX_LEVELS = 8;
 constexpr int MG_SMOOTH_DEG = 2;
-constexpr int MG_COARSE_DEG = 16;
+constexpr int MG_MAX_COARSE_DEG = 32;
+// tuning (environment, read at build): coarse grids keep at least
+// GM_MG_MIN_CELLS cells per direction (default 2); the coarsest level runs a
+// Chebyshev polynomial of degree GM_MG_COARSE_DEG (default 8)
+int mg_min_cells()
+{
+    const char* v = std::getenv("GM_MG_MIN_CELLS");
+    const int n = v ? std::atoi(v) : 2;
+    return n >= 1 ? n : 2;
+}
+int mg_coarse_deg()
+{
+    const char* v = std::getenv("GM_MG_COARSE_DEG");
+    const int n = v ? std::atoi(v) : 8;
+    return (n >= 1 && n <= MG_MAX_COARSE_DEG) ? n : 8;
+}
+
+// grid of a level's vector kernels: one thread per node up to the fixed grid
+int mg_blocks(long long N)
+{
+    const long long b = (N + 255) / 256;
+    return (int)(b < GM_RED_BLOCKS ? b : GM_RED_BLOCKS);
+}
 
 __device__ inline void mg_plane(const GridDesc& g, int kk, int* o, int* up)
 {
@@ -238,7 +260,8 @@ PairPrec<float> level_pairs(gm_ctx* x)
 bool coarsenable(const gm_ctx* x)
 {
     if (x->nx % 2 || x->ny % 2 || x->nz % 2) return false;
-    if (x->nx / 2 < MG_MIN_CELLS || x->ny / 2 < MG_MIN_CELLS || x->nz / 2 < MG_MIN_CELLS) return false;
+    const int mc = mg_min_cells();
+    if (x->nx / 2 < mc || x->ny / 2 < mc || x->nz / 2 < mc) return false;
     if (x->has_fault) {
         if (x->kf_orig % 2) return false;
         if (x->kf_orig / 2 < 1 || (x->nz - x->kf_orig) / 2 < 1) return false;
@@ -308,7 +331,7 @@ int cheb_step(gm_ctx* c, const MGLevel& L, int k, bool xzero, const int* skip, c
 {
     gm_ctx* x = L.cx;
     const double* cf = c->mg_coef.as<double>() + 2 * (L.coef_off + k);
-    mg_cheb_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(x->N, L.b, xzero ? nullptr : L.y, L.x, L.d,
+    mg_cheb_kernel<<<mg_blocks(x->N), 256, 0, s>>>(x->N, L.b, xzero ? nullptr : L.y, L.x, L.d,
                                                  x->dKinv32.as<float>(), level_pairs(x), cf, xzero ? 1 : 0, skip);
     GM_LAUNCHED(c);
     return GM_OK;
@@ -453,7 +476,7 @@ int build(gm_ctx* c)
     c->mg[0].y = c->mg_y0.as<float>();
     // coefficient slot 0 = (0, 1) for the eigenvalue estimate; levels follow
     std::vector<double> coef = {0.0, 1.0};
-    GM_CUDA_TRY(c, c->mg_coef.alloc(2 * sizeof(double) * (1 + MG_MAX_LEVELS * MG_COARSE_DEG)));
+    GM_CUDA_TRY(c, c->mg_coef.alloc(2 * sizeof(double) * (1 + MG_MAX_LEVELS * MG_MAX_COARSE_DEG)));
     GM_CUDA_TRY(c, cudaMemcpy(c->mg_coef.p, coef.data(), 2 * sizeof(double), cudaMemcpyHostToDevice));
     int rc;
     if ((rc = inject_and_refresh(c, 0))) { gm_mg_release(c); return rc; }
@@ -468,7 +491,7 @@ int build(gm_ctx* c)
     for (size_t l = 0; l < c->mg.size(); ++l) {
         MGLevel& L = c->mg[l];
         const bool last = l + 1 == c->mg.size();
-        L.deg = last ? MG_COARSE_DEG : MG_SMOOTH_DEG;
+        L.deg = last ? mg_coarse_deg() : MG_SMOOTH_DEG;
         L.coef_off = off;
         const double hi = 1.15 * L.lmax;
         cheb_coefs(last ? 0.01 * hi : 0.25 * L.lmax, hi, L.deg, coef);
