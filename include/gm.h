@@ -236,14 +236,14 @@ int gm_set_permeability(gm_ctx* ctx, const double* k_host, int64_t n);
  * return map.  Synchronises. */
 int gm_set_friction(gm_ctx* ctx, const double* f_host, int64_t n);
 
-/* Preconditioner of the FP32 K_T inner solves (the paper leaves the inner
- * solvers open, Sec. 3.3.2).  kind 0: block Jacobi, 3x3 nodal blocks and 6x6
- * blocks for the two lips of each fault pair.  kind 1 (default): one geometric
- * multigrid V-cycle (grids halved within each fault block, Chebyshev-smoothed
- * with that block Jacobi), built on first use (its set-up synchronises);
- * grids whose cell counts or fault index cannot be halved keep kind 0.  FP64 solves always use kind 0.
- * The converged solutions agree to the solver tolerances.  GM_EINVAL for
- * another kind. */
+/* Preconditioner of the K_T inner solves, FP32 and FP64 (the paper leaves the
+ * inner solvers open, Sec. 3.3.2).  kind 0: block Jacobi, 3x3 nodal blocks and
+ * 6x6 blocks for the two lips of each fault pair.  kind 1 (default): one
+ * geometric multigrid V-cycle (grids halved within each fault block,
+ * Chebyshev-smoothed with that block Jacobi), built on first use (its set-up
+ * synchronises); grids whose cell counts or fault index cannot be halved keep
+ * kind 0.  The converged solutions agree to the solver tolerances.  GM_EINVAL
+ * for another kind. */
 int gm_set_preconditioner(gm_ctx* ctx, int kind);
 
 /* Per-pair in-situ fault tractions, for in-situ stress that varies over the

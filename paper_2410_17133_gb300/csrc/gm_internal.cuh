@@ -234,6 +234,10 @@ struct MGLevel {
     float* x = nullptr;
     float* d = nullptr;      // Chebyshev direction
     float* y = nullptr;      // operator output
+    double* b64 = nullptr;   // the same vectors for FP64 solves
+    double* x64 = nullptr;
+    double* d64 = nullptr;
+    double* y64 = nullptr;
     double lmax = 0.0;       // largest eigenvalue estimate of M^-1 K_T
     int deg = 2;             // Chebyshev degree of the smoother (of the solve on the coarsest level)
     int coef_off = 0;        // first (c1, c2) pair of this level in mg_coef
@@ -290,6 +294,7 @@ struct gm_ctx {
     int precond = 1;                                   // FP32 K_T solves: 0 block Jacobi, 1 multigrid
     std::vector<MGLevel> mg;                           // built on first use
     DevBuf mg_d0, mg_y0, mg_coef;                      // level-0 smoother vectors, Chebyshev coefficients
+    DevBuf mg_d0_64, mg_y0_64;                         // level-0 smoother vectors of FP64 solves
     DevBuf dFS64, dFS32, dAfsinv64, dAfsinv32;         // fixed-stress storage term
     DevBuf dscal;                                      // PcgScalars[4] + misc
     DevBuf dpart;                                      // reduction partials
@@ -308,11 +313,11 @@ struct gm_ctx {
     // CUDA graphs of two fused PCG iterations, per (operator, precision);
     // captured on a private stream, replayed on the caller's stream
     cudaStream_t cap_stream = nullptr;
-    // [which][0: FP64, 1: FP32, 2: FP32 with the multigrid preconditioner]
-    cudaGraphExec_t pcg_graph[3][3] = {};
-    double pcg_graph_dt[3][3] = {};
-    int pcg_graph_maxit[3][3] = {};
-    long long pcg_graph_launches[3][3] = {};
+    // [which][0: FP64, 1: FP32, 2: FP32 with the multigrid preconditioner, 3: FP64 with it]
+    cudaGraphExec_t pcg_graph[3][4] = {};
+    double pcg_graph_dt[3][4] = {};
+    int pcg_graph_maxit[3][4] = {};
+    long long pcg_graph_launches[3][4] = {};
     bool use_graphs = true;
     void drop_graphs() {
         for (auto& row : pcg_graph)
@@ -364,12 +369,13 @@ int gm_launch_residual(gm_ctx* c, const double* y1u, const double* y1p, const do
 int gm_launch_diag(gm_ctx* c, cudaStream_t s);            // dK (bulk), dA (needs dt)
 int gm_launch_block_jacobi(gm_ctx* c, cudaStream_t s);    // K_T 3x3 inverse blocks
 // multigrid preconditioner of the FP32 K_T solves (gm_mg.cu)
-int gm_mg_prepare(gm_ctx* c, cudaStream_t s);     // GM_EINVAL: grid not coarsenable (caller falls back)
-int gm_mg_vcycle(gm_ctx* c, const float* r, float* z, const int* skip, cudaStream_t s);
+int gm_mg_prepare(gm_ctx* c, int prec, cudaStream_t s);   // GM_EINVAL: grid not coarsenable (caller falls back)
+int gm_mg_vcycle(gm_ctx* c, int prec, const void* r, void* z, const int* skip, cudaStream_t s);
 void gm_mg_release(gm_ctx* c);
-int gm_launch_pcg_update_noz(gm_ctx* c, float* x, float* r, const float* p, const float* q, PcgScalars* sc,
-                             int maxit, cudaStream_t s);
-int gm_launch_pcg_rz(gm_ctx* c, const float* r, const float* z, PcgScalars* sc, int init, cudaStream_t s);
+int gm_launch_pcg_update_noz(gm_ctx* c, int prec, void* x, void* r, const void* p, const void* q,
+                             PcgScalars* sc, int maxit, cudaStream_t s);
+int gm_launch_pcg_rz(gm_ctx* c, int prec, const void* r, const void* z, PcgScalars* sc, int init,
+                     cudaStream_t s);
 int gm_launch_count_changes(gm_ctx* c, const int8_t* a, const int8_t* b, int* out, cudaStream_t s);
 
 // Linear algebra

@@ -431,17 +431,18 @@ int gm_launch_jacobi_apply(gm_ctx* c, int which, const double* r, double* z, cud
 // PCG steps around the multigrid preconditioner (FP32 K_T solves): the update
 // pass leaves z to the V-cycle, and a second pass forms r.z and beta.
 // ---------------------------------------------------------------------------
+template <typename T>
 __global__ void __launch_bounds__(256)
-gm_pcg_update_noz_kernel(long long n, float* x, float* r, const float* p, const float* q, PcgScalars* sc,
-                         int maxit, RedCtx rc)
+gm_pcg_update_noz_kernel(long long n, T* x, T* r, const T* p, const T* q, PcgScalars* sc, int maxit,
+                         RedCtx rc)
 {
     if (sc->done) return;
-    const float alpha = (float)sc->alpha;
+    const T alpha = (T)sc->alpha;
     double v[1] = {0.0};
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        x[i] = fmaf(alpha, p[i], x[i]);
-        const float ri = fmaf(-alpha, q[i], r[i]);
+        x[i] = fma(alpha, p[i], x[i]);
+        const T ri = fma(-alpha, q[i], r[i]);
         r[i] = ri;
         v[0] += (double)ri * (double)ri;
     }
@@ -460,8 +461,9 @@ gm_pcg_update_noz_kernel(long long n, float* x, float* r, const float* p, const 
     }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(256)
-gm_pcg_rz_kernel(long long n, const float* r, const float* z, PcgScalars* sc, int init, RedCtx rc)
+gm_pcg_rz_kernel(long long n, const T* r, const T* z, PcgScalars* sc, int init, RedCtx rc)
 {
     if (sc->done) return;
     double v[1] = {0.0};
@@ -481,17 +483,28 @@ gm_pcg_rz_kernel(long long n, const float* r, const float* z, PcgScalars* sc, in
     }
 }
 
-int gm_launch_pcg_update_noz(gm_ctx* c, float* x, float* r, const float* p, const float* q, PcgScalars* sc,
-                             int maxit, cudaStream_t s)
+int gm_launch_pcg_update_noz(gm_ctx* c, int prec, void* x, void* r, const void* p, const void* q,
+                             PcgScalars* sc, int maxit, cudaStream_t s)
 {
-    gm_pcg_update_noz_kernel<<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(3 * c->N, x, r, p, q, sc, maxit, redctx(c));
+    if (prec == GM_F64)
+        gm_pcg_update_noz_kernel<double><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
+            3 * c->N, (double*)x, (double*)r, (const double*)p, (const double*)q, sc, maxit, redctx(c));
+    else
+        gm_pcg_update_noz_kernel<float><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(
+            3 * c->N, (float*)x, (float*)r, (const float*)p, (const float*)q, sc, maxit, redctx(c));
     GM_LAUNCHED(c);
     return GM_OK;
 }
 
-int gm_launch_pcg_rz(gm_ctx* c, const float* r, const float* z, PcgScalars* sc, int init, cudaStream_t s)
+int gm_launch_pcg_rz(gm_ctx* c, int prec, const void* r, const void* z, PcgScalars* sc, int init,
+                     cudaStream_t s)
 {
-    gm_pcg_rz_kernel<<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(3 * c->N, r, z, sc, init, redctx(c));
+    if (prec == GM_F64)
+        gm_pcg_rz_kernel<double><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(3 * c->N, (const double*)r,
+                                                                        (const double*)z, sc, init, redctx(c));
+    else
+        gm_pcg_rz_kernel<float><<<GM_RED_BLOCKS, GM_RED_THREADS, 0, s>>>(3 * c->N, (const float*)r,
+                                                                       (const float*)z, sc, init, redctx(c));
     GM_LAUNCHED(c);
     return GM_OK;
 }

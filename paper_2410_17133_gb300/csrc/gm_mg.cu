@@ -64,7 +64,8 @@ __device__ inline int mg_ext(const GridDesc& g, int o, int up) { return (g.kf >=
 
 // b_c = R (b_f - y_f): full weighting inside each block; constrained coarse
 // components 0.  y_f may be null (then r_f = b_f).
-__global__ void mg_restrict_kernel(GridDesc F, GridDesc Cg, const float* bf, const float* yf, float* bc,
+template <typename T>
+__global__ void mg_restrict_kernel(GridDesc F, GridDesc Cg, const T* bf, const T* yf, T* bc,
                                    const uint8_t* maskc, const int* skip)
 {
     if (skip && *skip) return;
@@ -77,37 +78,38 @@ __global__ void mg_restrict_kernel(GridDesc F, GridDesc Cg, const float* bf, con
     mg_plane(Cg, kkc, &oc, &up);
     const int olo = (F.kf >= 0 && up) ? F.kf : 0;
     const int ohi = (F.kf >= 0 && !up) ? F.kf : F.nz;
-    float acc[3] = {0.f, 0.f, 0.f};
+    T acc[3] = {T(0), T(0), T(0)};
     for (int dk = -1; dk <= 1; ++dk) {
         const int o = 2 * oc + dk;
         if (o < olo || o > ohi) continue;
-        const float wz = dk ? 0.5f : 1.f;
+        const T wz = dk ? T(0.5) : T(1);
         const long long kk = mg_ext(F, o, up);
         for (int dj = -1; dj <= 1; ++dj) {
             const int j = 2 * jc + dj;
             if (j < 0 || j > F.ny) continue;
-            const float wy = dj ? 0.5f : 1.f;
+            const T wy = dj ? T(0.5) : T(1);
             for (int di = -1; di <= 1; ++di) {
                 const int i = 2 * ic + di;
                 if (i < 0 || i > F.nx) continue;
-                const float w = wz * wy * (di ? 0.5f : 1.f);
+                const T w = wz * wy * (di ? T(0.5) : T(1));
                 const long long f = i + (long long)(F.nx + 1) * (j + (long long)(F.ny + 1) * kk);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float r = bf[c * F.N + f] - (yf ? yf[c * F.N + f] : 0.f);
-                    acc[c] = fmaf(w, r, acc[c]);
+                    const T r = bf[c * F.N + f] - (yf ? yf[c * F.N + f] : T(0));
+                    acc[c] = fma(w, r, acc[c]);
                 }
             }
         }
     }
     const unsigned m = maskc[nc];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) bc[c * Cg.N + nc] = ((m >> c) & 1u) ? 0.f : acc[c];
+    for (int c = 0; c < 3; ++c) bc[c * Cg.N + nc] = ((m >> c) & 1u) ? T(0) : acc[c];
 }
 
 // x_f += P x_c: trilinear interpolation inside each block; constrained fine
 // components unchanged.
-__global__ void mg_prolong_kernel(GridDesc F, GridDesc Cg, const float* xc, float* xf, const uint8_t* maskf,
+template <typename T>
+__global__ void mg_prolong_kernel(GridDesc F, GridDesc Cg, const T* xc, T* xf, const uint8_t* maskf,
                                   const int* skip)
 {
     if (skip && *skip) return;
@@ -119,20 +121,20 @@ __global__ void mg_prolong_kernel(GridDesc F, GridDesc Cg, const float* xc, floa
     int o, up;
     mg_plane(F, kk, &o, &up);
     int pi[2], pj[2], po[2];
-    float wi[2], wj[2], wo[2];
+    T wi[2], wj[2], wo[2];
     const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, no = (o & 1) ? 2 : 1;
-    pi[0] = i >> 1; pi[1] = (i + 1) >> 1; wi[0] = wi[1] = (i & 1) ? 0.5f : 1.f;
-    pj[0] = j >> 1; pj[1] = (j + 1) >> 1; wj[0] = wj[1] = (j & 1) ? 0.5f : 1.f;
-    po[0] = o >> 1; po[1] = (o + 1) >> 1; wo[0] = wo[1] = (o & 1) ? 0.5f : 1.f;
-    float acc[3] = {0.f, 0.f, 0.f};
+    pi[0] = i >> 1; pi[1] = (i + 1) >> 1; wi[0] = wi[1] = (i & 1) ? T(0.5) : T(1);
+    pj[0] = j >> 1; pj[1] = (j + 1) >> 1; wj[0] = wj[1] = (j & 1) ? T(0.5) : T(1);
+    po[0] = o >> 1; po[1] = (o + 1) >> 1; wo[0] = wo[1] = (o & 1) ? T(0.5) : T(1);
+    T acc[3] = {T(0), T(0), T(0)};
     for (int a = 0; a < no; ++a) {
         const long long kkc = mg_ext(Cg, po[a], up);
         for (int b = 0; b < nj; ++b)
             for (int e = 0; e < ni; ++e) {
-                const float w = wo[a] * wj[b] * wi[e];
+                const T w = wo[a] * wj[b] * wi[e];
                 const long long nc = pi[e] + (long long)(Cg.nx + 1) * (pj[b] + (long long)(Cg.ny + 1) * kkc);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) acc[c] = fmaf(w, xc[c * Cg.N + nc], acc[c]);
+                for (int c = 0; c < 3; ++c) acc[c] = fma(w, xc[c * Cg.N + nc], acc[c]);
             }
     }
     const unsigned m = maskf[f];
@@ -158,25 +160,26 @@ __global__ void mg_inject_d_kernel(GridDesc F, GridDesc Cg, const double* d64f, 
 
 // One Chebyshev step: r = b - y (y null: x = 0, r = b), z = M^-1 r,
 // d = c1 d + c2 z (c1 = 0: d = c2 z), x = x + d (xzero: x = d).
-__global__ void __launch_bounds__(256) mg_cheb_kernel(long long N, const float* b, const float* y, float* x,
-                                                      float* d, const float* mi, PairPrec<float> pp,
-                                                      const double* coef, int xzero, const int* skip)
+template <typename T>
+__global__ void __launch_bounds__(256) mg_cheb_kernel(long long N, const T* b, const T* y, T* x, T* d,
+                                                      const T* mi, PairPrec<T> pp, const double* coef, int xzero,
+                                                      const int* skip)
 {
     if (skip && *skip) return;
-    const float c1 = (float)coef[0], c2 = (float)coef[1];
+    const T c1 = (T)coef[0], c2 = (T)coef[1];
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
         const long long dd = n - pp.lo;
         if (pp.inv != nullptr && dd >= 0 && dd < 2 * pp.nb) {
             if (dd >= pp.nb) continue;                 // upper lip: done with its pair
             const long long nd[2] = {n, n + pp.nb};
-            float r6[6], z6[6];
+            T r6[6], z6[6];
 #pragma unroll
             for (int s = 0; s < 2; ++s)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     const long long k = c * N + nd[s];
-                    r6[3 * s + c] = b[k] - (y ? y[k] : 0.f);
+                    r6[3 * s + c] = b[k] - (y ? y[k] : T(0));
                 }
             gm_pair_apply(pp, dd, r6, z6);
 #pragma unroll
@@ -184,20 +187,20 @@ __global__ void __launch_bounds__(256) mg_cheb_kernel(long long N, const float* 
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     const long long k = c * N + nd[s];
-                    const float dn = c1 == 0.f ? c2 * z6[3 * s + c] : fmaf(c1, d[k], c2 * z6[3 * s + c]);
+                    const T dn = c1 == T(0) ? c2 * z6[3 * s + c] : fma(c1, d[k], c2 * z6[3 * s + c]);
                     d[k] = dn;
                     x[k] = xzero ? dn : x[k] + dn;
                 }
             continue;
         }
-        float r[3], z[3];
+        T r[3], z[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) r[c] = b[c * N + n] - (y ? y[c * N + n] : 0.f);
-        Prec<float, 0>::apply(mi, N, n, r, z);
+        for (int c = 0; c < 3; ++c) r[c] = b[c * N + n] - (y ? y[c * N + n] : T(0));
+        Prec<T, 0>::apply(mi, N, n, r, z);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const long long k = c * N + n;
-            const float dn = c1 == 0.f ? c2 * z[c] : fmaf(c1, d[k], c2 * z[c]);
+            const T dn = c1 == T(0) ? c2 * z[c] : fma(c1, d[k], c2 * z[c]);
             d[k] = dn;
             x[k] = xzero ? dn : x[k] + dn;
         }
@@ -247,14 +250,33 @@ __global__ void mg_seed_kernel(long long N, const uint8_t* mask, float* v)
     }
 }
 
-PairPrec<float> level_pairs(gm_ctx* x)
+template <typename T>
+PairPrec<T> level_pairs(gm_ctx* x)
 {
-    PairPrec<float> pp{nullptr, x->g.nb, -1};
+    PairPrec<T> pp{nullptr, x->g.nb, -1};
     if (x->g.kf >= 0 && x->pair_prec) {
-        pp.inv = x->dKpair32.as<float>();
+        if constexpr (sizeof(T) == 8) pp.inv = x->dKpair64.as<T>();
+        else pp.inv = x->dKpair32.as<T>();
         pp.lo = (long long)x->g.kf * x->g.nb;
     }
     return pp;
+}
+
+template <typename T>
+const T* level_inv(gm_ctx* x)
+{
+    if constexpr (sizeof(T) == 8) return x->dKinv64.as<T>();
+    else return x->dKinv32.as<T>();
+}
+
+// the level's vectors in the solve precision
+template <typename T>
+struct LV { T* b; T* x; T* d; T* y; };
+template <typename T>
+LV<T> lv(const MGLevel& L)
+{
+    if constexpr (sizeof(T) == 8) return LV<T>{L.b64, L.x64, L.d64, L.y64};
+    else return LV<T>{L.b, L.x, L.d, L.y};
 }
 
 bool coarsenable(const gm_ctx* x)
@@ -326,45 +348,56 @@ int apply_kt(gm_ctx* x, const float* v, float* y, const int* skip, cudaStream_t 
 {
     return gm_launch_apply_f32(x, GM_MODE_KT, 1.0, 0.0, 0.0, 0.0, 0.0, v, nullptr, y, nullptr, s, skip);
 }
+int apply_kt(gm_ctx* x, const double* v, double* y, const int* skip, cudaStream_t s)
+{
+    return gm_launch_apply_f64(x, GM_MODE_KT, 1.0, 0.0, 0.0, 0.0, 0.0, v, nullptr, y, nullptr, s, skip);
+}
 
+template <typename T>
 int cheb_step(gm_ctx* c, const MGLevel& L, int k, bool xzero, const int* skip, cudaStream_t s)
 {
     gm_ctx* x = L.cx;
+    const LV<T> v = lv<T>(L);
     const double* cf = c->mg_coef.as<double>() + 2 * (L.coef_off + k);
-    mg_cheb_kernel<<<mg_blocks(x->N), 256, 0, s>>>(x->N, L.b, xzero ? nullptr : L.y, L.x, L.d,
-                                                 x->dKinv32.as<float>(), level_pairs(x), cf, xzero ? 1 : 0, skip);
+    mg_cheb_kernel<T><<<mg_blocks(x->N), 256, 0, s>>>(x->N, v.b, xzero ? nullptr : v.y, v.x, v.d, level_inv<T>(x),
+                                                    level_pairs<T>(x), cf, xzero ? 1 : 0, skip);
     GM_LAUNCHED(c);
     return GM_OK;
 }
 
 // deg Chebyshev steps on level L (from x = 0 if xzero)
+template <typename T>
 int smooth(gm_ctx* c, const MGLevel& L, int deg, bool xzero, const int* skip, cudaStream_t s)
 {
+    const LV<T> v = lv<T>(L);
     int rc;
     for (int k = 0; k < deg; ++k) {
         const bool z0 = xzero && k == 0;
-        if (!z0 && (rc = apply_kt(L.cx, L.x, L.y, skip, s))) return rc;
-        if ((rc = cheb_step(c, L, k, z0, skip, s))) return rc;
+        if (!z0 && (rc = apply_kt(L.cx, v.x, v.y, skip, s))) return rc;
+        if ((rc = cheb_step<T>(c, L, k, z0, skip, s))) return rc;
     }
     return GM_OK;
 }
 
+template <typename T>
 int vcycle(gm_ctx* c, size_t l, const int* skip, cudaStream_t s)
 {
     const MGLevel& L = c->mg[l];
+    const LV<T> v = lv<T>(L);
     int rc;
-    if (l + 1 == c->mg.size()) return smooth(c, L, L.deg, true, skip, s);
-    if ((rc = smooth(c, L, L.deg, true, skip, s))) return rc;
-    if ((rc = apply_kt(L.cx, L.x, L.y, skip, s))) return rc;
+    if (l + 1 == c->mg.size()) return smooth<T>(c, L, L.deg, true, skip, s);
+    if ((rc = smooth<T>(c, L, L.deg, true, skip, s))) return rc;
+    if ((rc = apply_kt(L.cx, v.x, v.y, skip, s))) return rc;
     const MGLevel& C = c->mg[l + 1];
-    mg_restrict_kernel<<<(int)((C.cx->N + 255) / 256), 256, 0, s>>>(L.cx->g, C.cx->g, L.b, L.y, C.b,
-                                                                     C.cx->dmask.as<uint8_t>(), skip);
+    const LV<T> w = lv<T>(C);
+    mg_restrict_kernel<T><<<(int)((C.cx->N + 255) / 256), 256, 0, s>>>(L.cx->g, C.cx->g, v.b, v.y, w.b,
+                                                                        C.cx->dmask.as<uint8_t>(), skip);
     GM_LAUNCHED(c);
-    if ((rc = vcycle(c, l + 1, skip, s))) return rc;
-    mg_prolong_kernel<<<(int)((L.cx->N + 255) / 256), 256, 0, s>>>(L.cx->g, C.cx->g, C.x, L.x,
-                                                                    L.cx->dmask.as<uint8_t>(), skip);
+    if ((rc = vcycle<T>(c, l + 1, skip, s))) return rc;
+    mg_prolong_kernel<T><<<(int)((L.cx->N + 255) / 256), 256, 0, s>>>(L.cx->g, C.cx->g, w.x, v.x,
+                                                                       L.cx->dmask.as<uint8_t>(), skip);
     GM_LAUNCHED(c);
-    return smooth(c, L, L.deg, false, skip, s);
+    return smooth<T>(c, L, L.deg, false, skip, s);
 }
 
 // Chebyshev coefficients (c1, c2) of step k over [lo, hi] (Saad, Iterative
@@ -414,8 +447,8 @@ int estimate_lmax(gm_ctx* c, MGLevel& L)
     double lam = 0.0;
     for (int it = 0; it < 12; ++it) {
         if ((rc = apply_kt(x, v, L.y, nullptr, 0))) return rc;
-        mg_cheb_kernel<<<GM_RED_BLOCKS, 256>>>(x->N, L.y, nullptr, L.x, L.d, x->dKinv32.as<float>(),
-                                               level_pairs(x), unit, 1, nullptr);
+        mg_cheb_kernel<float><<<GM_RED_BLOCKS, 256>>>(x->N, L.y, nullptr, L.x, L.d, x->dKinv32.as<float>(),
+                                                      level_pairs<float>(x), unit, 1, nullptr);
         GM_LAUNCHED(c);
         double nw;
         if ((rc = norm2(c, n3, L.x, &nw))) return rc;
@@ -462,6 +495,10 @@ int build(gm_ctx* c)
         L.x = ch->k_x32.as<float>();
         L.d = ch->k_z32.as<float>();
         L.y = ch->k_q32.as<float>();
+        L.b64 = ch->k_r.as<double>();
+        L.x64 = ch->k_x64.as<double>();
+        L.d64 = ch->k_z.as<double>();
+        L.y64 = ch->k_q.as<double>();
         c->mg.push_back(L);
         cur = ch;
     }
@@ -510,28 +547,47 @@ void gm_mg_release(gm_ctx* c)
     c->mg.clear();
     c->mg_d0.release();
     c->mg_y0.release();
+    c->mg_d0_64.release();
+    c->mg_y0_64.release();
     c->mg_coef.release();
 }
 
-int gm_mg_prepare(gm_ctx* c, cudaStream_t s)
+int gm_mg_prepare(gm_ctx* c, int prec, cudaStream_t s)
 {
     if (c->mg.empty()) {
         // the one-time build runs on the default stream and reads the block
         // Jacobi that the caller may still be computing on s
         GM_CUDA_TRY(c, cudaStreamSynchronize(s));
-        return build(c);
+        if (int rc = build(c)) return rc;
+    } else if (int rc = inject_and_refresh(c, s)) {
+        return rc;
     }
-    return inject_and_refresh(c, s);
+    if (prec == GM_F64 && !c->mg_d0_64.p) {
+        GM_CUDA_TRY(c, cudaStreamSynchronize(s));
+        GM_CUDA_TRY(c, c->mg_d0_64.alloc(3 * c->N * sizeof(double)));
+        GM_CUDA_TRY(c, c->mg_y0_64.alloc(3 * c->N * sizeof(double)));
+        c->mg[0].d64 = c->mg_d0_64.as<double>();
+        c->mg[0].y64 = c->mg_y0_64.as<double>();
+    }
+    return GM_OK;
 }
 
-int gm_mg_vcycle(gm_ctx* c, const float* r, float* z, const int* skip, cudaStream_t s)
+int gm_mg_vcycle(gm_ctx* c, int prec, const void* r, void* z, const int* skip, cudaStream_t s)
 {
     if (c->mg.empty()) return c->set_err(GM_ESTATE, "multigrid: not prepared");
-    c->mg[0].b = const_cast<float*>(r);
-    c->mg[0].x = z;
+    if (prec == GM_F64 && !c->mg[0].d64) return c->set_err(GM_ESTATE, "multigrid: FP64 vectors not prepared");
     long long before = 0;
     for (size_t l = 1; l < c->mg.size(); ++l) before += c->mg[l].cx->launches;
-    const int rc = vcycle(c, 0, skip, s);
+    int rc;
+    if (prec == GM_F64) {
+        c->mg[0].b64 = static_cast<double*>(const_cast<void*>(r));
+        c->mg[0].x64 = static_cast<double*>(z);
+        rc = vcycle<double>(c, 0, skip, s);
+    } else {
+        c->mg[0].b = static_cast<float*>(const_cast<void*>(r));
+        c->mg[0].x = static_cast<float*>(z);
+        rc = vcycle<float>(c, 0, skip, s);
+    }
     long long after = 0;
     for (size_t l = 1; l < c->mg.size(); ++l) after += c->mg[l].cx->launches;
     c->launches += after - before;   // the coarse levels' kernels count as this context's

@@ -38,11 +38,11 @@ int gm_pcg(gm_ctx* c, int which, int prec, const double* b, double* x, double rt
     int rc;
     void *r, *z, *p, *p2, *q, *xx;
     const void* bb;
-    // FP32 K_T solves may be preconditioned by a multigrid V-cycle; a grid that
+    // K_T solves may be preconditioned by a multigrid V-cycle; a grid that
     // cannot be coarsened keeps the block-Jacobi preconditioner
-    bool use_mg = prec == GM_F32 && which == 0 && c->precond == 1;
+    bool use_mg = which == 0 && c->precond == 1;
     if (use_mg) {
-        rc = gm_mg_prepare(c, s);
+        rc = gm_mg_prepare(c, prec, s);
         if (rc == GM_EINVAL) use_mg = false;
         else if (rc) return rc;
     }
@@ -89,11 +89,11 @@ int gm_pcg(gm_ctx* c, int which, int prec, const double* b, double* x, double rt
         GM_CUDA_TRY(c, cudaMemsetAsync(xx, 0, n * sizeof(float), s));
         bb = b32;
         if ((rc = gm_launch_pcg_init(c, which, GM_F32, bb, nullptr, r, z, p, rtol, sc, s))) return rc;
-        if (use_mg) {
-            // z = V(r) replaces the block-Jacobi z of the init pass
-            if ((rc = gm_mg_vcycle(c, (const float*)r, (float*)z, &sc->done, s))) return rc;
-            if ((rc = gm_launch_pcg_rz(c, (const float*)r, (const float*)z, sc, 1, s))) return rc;
-        }
+    }
+    if (use_mg) {
+        // z = V(r) replaces the block-Jacobi z of the init pass
+        if ((rc = gm_mg_vcycle(c, prec, r, z, &sc->done, s))) return rc;
+        if ((rc = gm_launch_pcg_rz(c, prec, r, z, sc, 1, s))) return rc;
     }
     PcgScalars* hs = static_cast<PcgScalars*>(c->hpin);
     int batch = 4;
@@ -112,10 +112,9 @@ int gm_pcg(gm_ctx* c, int which, int prec, const double* b, double* x, double rt
                                             (float*)pnew, (float*)q, sc, st);
             if (e) return e;
             if (use_mg) {
-                if ((e = gm_launch_pcg_update_noz(c, (float*)xx, (float*)r, (const float*)pnew, (const float*)q,
-                                                  sc, maxit, st))) return e;
-                if ((e = gm_mg_vcycle(c, (const float*)r, (float*)z, &sc->done, st))) return e;
-                if ((e = gm_launch_pcg_rz(c, (const float*)r, (const float*)z, sc, 0, st))) return e;
+                if ((e = gm_launch_pcg_update_noz(c, prec, xx, r, pnew, q, sc, maxit, st))) return e;
+                if ((e = gm_mg_vcycle(c, prec, r, z, &sc->done, st))) return e;
+                if ((e = gm_launch_pcg_rz(c, prec, r, z, sc, 0, st))) return e;
                 continue;
             }
             if ((e = gm_launch_pcg_update(c, which, prec, xx, r, z, pnew, q, sc, maxit, st))) return e;
@@ -123,7 +122,7 @@ int gm_pcg(gm_ctx* c, int which, int prec, const double* b, double* x, double rt
         return GM_OK;
     };
     cudaGraphExec_t gexec = nullptr;
-    const int pi = prec == GM_F64 ? 0 : (use_mg ? 2 : 1);
+    const int pi = prec == GM_F64 ? (use_mg ? 3 : 0) : (use_mg ? 2 : 1);
     if (c->use_graphs) {
         // the graph bakes in the kernel parameters: dt (A22 operators), maxit and
         // the solution pointer; rebuild when any of them changes
