@@ -44,3 +44,24 @@ int gm_launch_pcg_apply_f32(gm_ctx* c, int which, const float* z, const float* p
     if (e != cudaSuccess) return c->set_err(GM_ECUDA, std::string("pcg apply launch: ") + cudaGetErrorString(e));
     return GM_OK;
 }
+
+// Bulk part of K_T alone (no fault-kernel launch): y = K_b x.  The multigrid
+// smoother adds the cohesive term of the lip pairs itself.
+int gm_launch_bulk_k_f32(gm_ctx* c, const float* x, float* y, cudaStream_t s, const int* skip)
+{
+    int gx, gy, gz, zchunk;
+    gm_bulk_geometry(c, &gx, &gy, &gz, &zchunk);
+    BulkArgs<float> b = gm_bulk_args<float>(c, 1.0, 0.0, 0.0, 0.0, 0.0, c->dE32.as<float>(), c->dK32.as<float>());
+    b.zchunk = zchunk;
+    b.xu = x; b.xp = nullptr; b.yu = y; b.yp = nullptr;
+    b.skip = skip;
+    const dim3 grid(gx, gy, gz);
+    switch (c->cls) {
+    case GM_CLS_BOX: gm_bulk_apply_kernel<float, GM_CLS_BOX, GM_M_K, false><<<grid, 256, 0, s>>>(b, c->R32); break;
+    case GM_CLS_MONO: gm_bulk_apply_kernel<float, GM_CLS_MONO, GM_M_K, false><<<grid, 256, 0, s>>>(b, c->R32); break;
+    default: gm_bulk_apply_kernel<float, GM_CLS_GEN, GM_M_K, false><<<grid, 256, 0, s>>>(b, c->R32); break;
+    }
+    c->applies++;
+    GM_LAUNCHED(c);
+    return GM_OK;
+}

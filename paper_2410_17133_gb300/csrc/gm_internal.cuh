@@ -369,6 +369,8 @@ int gm_launch_residual(gm_ctx* c, const double* y1u, const double* y1p, const do
 int gm_launch_diag(gm_ctx* c, cudaStream_t s);            // dK (bulk), dA (needs dt)
 int gm_launch_block_jacobi(gm_ctx* c, cudaStream_t s);    // K_T 3x3 inverse blocks
 // multigrid preconditioner of the FP32 K_T solves (gm_mg.cu)
+int gm_launch_bulk_k_f32(gm_ctx* c, const float* x, float* y, cudaStream_t s, const int* skip);
+int gm_launch_bulk_k_f64(gm_ctx* c, const double* x, double* y, cudaStream_t s, const int* skip);
 int gm_mg_prepare(gm_ctx* c, int prec, cudaStream_t s);   // GM_EINVAL: grid not coarsenable (caller falls back)
 int gm_mg_vcycle(gm_ctx* c, int prec, const void* r, void* z, const int* skip, cudaStream_t s);
 void gm_mg_release(gm_ctx* c);

@@ -158,12 +158,23 @@ __global__ void mg_inject_d_kernel(GridDesc F, GridDesc Cg, const double* d64f, 
     }
 }
 
+// Cohesive term of K_T for the smoother (FaultK.D null: y already holds it).
+template <typename T>
+struct FaultK {
+    const T* D;            // 6 per pair (symmetric 3x3), or null
+    const uint8_t* mask;
+    T Aq;                  // area of one fault quad
+    int nx, ny;
+};
+
 // One Chebyshev step: r = b - y (y null: x = 0, r = b), z = M^-1 r,
-// d = c1 d + c2 z (c1 = 0: d = c2 z), x = x + d (xzero: x = d).
+// d = c1 d + c2 z (c1 = 0: d = c2 z), x = x + d (xzero: x = d).  With fk.D
+// set, y holds the bulk product only and the pair thread adds
+// +-A_i D [[x]] to the two lips first (the fault rows of K_T).
 template <typename T>
 __global__ void __launch_bounds__(256) mg_cheb_kernel(long long N, const T* b, const T* y, T* x, T* d,
                                                       const T* mi, PairPrec<T> pp, const double* coef, int xzero,
-                                                      const int* skip)
+                                                      const int* skip, FaultK<T> fk)
 {
     if (skip && *skip) return;
     const T c1 = (T)coef[0], c2 = (T)coef[1];
@@ -181,6 +192,31 @@ __global__ void __launch_bounds__(256) mg_cheb_kernel(long long N, const T* b, c
                     const long long k = c * N + nd[s];
                     r6[3 * s + c] = b[k] - (y ? y[k] : T(0));
                 }
+            if (fk.D != nullptr && y != nullptr) {
+                const int pi = (int)(dd % (fk.nx + 1)), pj = (int)(dd / (fk.nx + 1));
+                const int nqi = (pi > 0) + (pi < fk.nx), nqj = (pj > 0) + (pj < fk.ny);
+                const T Ai = fk.Aq * T(0.25) * T(nqi * nqj);
+                const unsigned mm = fk.mask[nd[0]], mp = fk.mask[nd[1]];
+                T j3[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const T up = ((mp >> c) & 1u) ? T(0) : x[c * N + nd[1]];
+                    const T um = ((mm >> c) & 1u) ? T(0) : x[c * N + nd[0]];
+                    j3[c] = up - um;
+                }
+                const T* D = fk.D;
+                const long long P = pp.nb;
+                const T d00 = D[dd], d01 = D[P + dd], d02 = D[2 * P + dd];
+                const T d11 = D[3 * P + dd], d12 = D[4 * P + dd], d22 = D[5 * P + dd];
+                const T f[3] = {Ai * (d00 * j3[0] + d01 * j3[1] + d02 * j3[2]),
+                                Ai * (d01 * j3[0] + d11 * j3[1] + d12 * j3[2]),
+                                Ai * (d02 * j3[0] + d12 * j3[1] + d22 * j3[2])};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (!((mm >> c) & 1u)) r6[c] += f[c];        // y_- -= f
+                    if (!((mp >> c) & 1u)) r6[3 + c] -= f[c];    // y_+ += f
+                }
+            }
             gm_pair_apply(pp, dd, r6, z6);
 #pragma unroll
             for (int s = 0; s < 2; ++s)
@@ -353,28 +389,56 @@ int apply_kt(gm_ctx* x, const double* v, double* y, const int* skip, cudaStream_
     return gm_launch_apply_f64(x, GM_MODE_KT, 1.0, 0.0, 0.0, 0.0, 0.0, v, nullptr, y, nullptr, s, skip);
 }
 
+int apply_kb(gm_ctx* x, const float* v, float* y, const int* skip, cudaStream_t s)
+{
+    return gm_launch_bulk_k_f32(x, v, y, s, skip);
+}
+int apply_kb(gm_ctx* x, const double* v, double* y, const int* skip, cudaStream_t s)
+{
+    return gm_launch_bulk_k_f64(x, v, y, s, skip);
+}
+
 template <typename T>
-int cheb_step(gm_ctx* c, const MGLevel& L, int k, bool xzero, const int* skip, cudaStream_t s)
+FaultK<T> level_fault(gm_ctx* x)
+{
+    FaultK<T> fk{nullptr, x->dmask.as<uint8_t>(), T(x->Aq), x->nx, x->ny};
+    // with lip-pair blocks every pair has one thread that can add its rows
+    if (x->g.kf >= 0 && x->pair_prec) {
+        if constexpr (sizeof(T) == 8) fk.D = x->dD64.as<T>();
+        else fk.D = x->dD32.as<T>();
+    }
+    return fk;
+}
+
+template <typename T>
+int cheb_step(gm_ctx* c, const MGLevel& L, int k, bool xzero, bool fused, const int* skip, cudaStream_t s)
 {
     gm_ctx* x = L.cx;
     const LV<T> v = lv<T>(L);
     const double* cf = c->mg_coef.as<double>() + 2 * (L.coef_off + k);
+    FaultK<T> fk = level_fault<T>(x);
+    if (!fused) fk.D = nullptr;
     mg_cheb_kernel<T><<<mg_blocks(x->N), 256, 0, s>>>(x->N, v.b, xzero ? nullptr : v.y, v.x, v.d, level_inv<T>(x),
-                                                    level_pairs<T>(x), cf, xzero ? 1 : 0, skip);
+                                                    level_pairs<T>(x), cf, xzero ? 1 : 0, skip, fk);
     GM_LAUNCHED(c);
     return GM_OK;
 }
 
-// deg Chebyshev steps on level L (from x = 0 if xzero)
+// deg Chebyshev steps on level L (from x = 0 if xzero).  The operator products
+// are bulk-only launches when the smoother adds the fault rows itself.
 template <typename T>
 int smooth(gm_ctx* c, const MGLevel& L, int deg, bool xzero, const int* skip, cudaStream_t s)
 {
     const LV<T> v = lv<T>(L);
+    const bool fused = level_fault<T>(L.cx).D != nullptr;
     int rc;
     for (int k = 0; k < deg; ++k) {
         const bool z0 = xzero && k == 0;
-        if (!z0 && (rc = apply_kt(L.cx, v.x, v.y, skip, s))) return rc;
-        if ((rc = cheb_step<T>(c, L, k, z0, skip, s))) return rc;
+        if (!z0) {
+            rc = fused ? apply_kb(L.cx, v.x, v.y, skip, s) : apply_kt(L.cx, v.x, v.y, skip, s);
+            if (rc) return rc;
+        }
+        if ((rc = cheb_step<T>(c, L, k, z0, fused, skip, s))) return rc;
     }
     return GM_OK;
 }
@@ -447,8 +511,10 @@ int estimate_lmax(gm_ctx* c, MGLevel& L)
     double lam = 0.0;
     for (int it = 0; it < 12; ++it) {
         if ((rc = apply_kt(x, v, L.y, nullptr, 0))) return rc;
+        FaultK<float> nofk = level_fault<float>(x);
+        nofk.D = nullptr;
         mg_cheb_kernel<float><<<GM_RED_BLOCKS, 256>>>(x->N, L.y, nullptr, L.x, L.d, x->dKinv32.as<float>(),
-                                                      level_pairs<float>(x), unit, 1, nullptr);
+                                                      level_pairs<float>(x), unit, 1, nullptr, nofk);
         GM_LAUNCHED(c);
         double nw;
         if ((rc = norm2(c, n3, L.x, &nw))) return rc;

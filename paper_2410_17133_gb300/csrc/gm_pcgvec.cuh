@@ -68,9 +68,10 @@ struct PairPrec {
 template <typename T>
 __device__ inline void gm_pair_apply(const PairPrec<T>& pp, long long d, const T (&r6)[6], T (&z6)[6])
 {
-    // rows one at a time: the pair path is taken by one thread per fault pair
-    // and must not raise the register budget of the node path
-#pragma unroll 1
+    // three rows at a time: the pair path is taken by one thread per fault
+    // pair; fully unrolled it would raise the register budget of the node
+    // path, one row at a time it waits for six memory round trips in a row
+#pragma unroll 3
     for (int a = 0; a < 6; ++a) {
         T acc = T(0);
 #pragma unroll
