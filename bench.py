@@ -340,7 +340,7 @@ def run_gm(args, rank, world, local_rank):
         roof = {"bound": "alu", "achieved": ach_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": frac_alu, "traffic": traffic, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                 "alt_hbm": {"achieved": ach_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": frac_hbm}}
-    roof["kernel"] = "gm_bulk_apply_kernel<float,K> (+ fault kernel), K_T apply"
+    roof["kernel"] = "gm_bulk_apply_kernel<float,K> (+ fault kernel): the K_T product on the finest grid, the largest per-launch cost; the multigrid smoother, summed over all grid levels, has the larger share of launches"
     roof["launch_ms"] = t32 * 1e3
     apply = {"KT_fp32_gdofs": 3 * N / t32 / 1e9, "KT_fp64_gdofs": 3 * N / t64 / 1e9,
              "KT_fp32_ms": t32 * 1e3, "KT_fp64_ms": t64 * 1e3,
