@@ -445,7 +445,7 @@ def implicit_step_fn():
     return ImplicitStep
 
 
-def run_with_adjoint(solver, dts, objective_grad, checkpoint_every=5, step_kw=None, rtol=1e-10):
+def run_with_adjoint(solver, dts, objective_grad, checkpoint_every=5, step_kw=None, rtol=1e-10, maxit=300):
     """Run len(dts) implicit steps from the solver's current state, then the
     reverse sweep of the multi-step adjoint (inelastic slip as history).
 
@@ -487,7 +487,7 @@ def run_with_adjoint(solver, dts, objective_grad, checkpoint_every=5, step_kw=No
             last = n == K
             lam, mu, fz, gk, gf, gq = solver.adjoint_sweep_step(
                 dJ_du if last else None, dJ_dp if last else None, dJ_dslip if last else None,
-                lam, mu, fz, rtol=rtol)
+                lam, mu, fz, rtol=rtol, maxit=maxit)
             g_logk += gk
             g_f += gf
             g_logQ += gq
