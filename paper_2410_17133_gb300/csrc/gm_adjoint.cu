@@ -209,7 +209,8 @@ int ensure_adjoint_buffers(gm_ctx* c, int m)
     if ((e = c->adj_V.alloc(v * (m + 1))) != cudaSuccess ||
         (e = c->adj_Z.alloc(v * m)) != cudaSuccess || (e = c->adj_w.alloc(v)) != cudaSuccess ||
         (e = c->adj_b.alloc(v)) != cudaSuccess || (e = c->adj_x.alloc(v)) != cudaSuccess ||
-        (e = c->adj_t.alloc(v)) != cudaSuccess)
+        (e = c->adj_t.alloc(v)) != cudaSuccess || (e = c->adj_s.alloc(v)) != cudaSuccess ||
+        (e = c->adj_u.alloc(v)) != cudaSuccess)
         return c->set_err(GM_ENOMEM, std::string("adjoint: cudaMalloc: ") + cudaGetErrorString(e));
     c->adj_m = m;
     return GM_OK;
@@ -225,6 +226,26 @@ int dot(gm_ctx* c, long long n, const double* x, const double* y, double* out, c
     GM_CUDA_TRY(c, cudaStreamSynchronize(s));
     *out = h[0];
     return GM_OK;
+}
+
+// Row/column scaling of the adjoint system: S = diag(K_b, A22)^(-1/2) (1 on
+// rows without a positive diagonal).  GMRES runs on S J^T S, so that force and
+// flow rows, whose units differ by many orders of magnitude on layered
+// problems, weigh alike in its residual norm.
+__global__ void adj_make_scale_kernel(long long N, const double* dK, const double* dA, double* S)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 4 * N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double d = i < 3 * N ? dK[i] : dA[i - 3 * N];
+        S[i] = d > 0.0 ? 1.0 / sqrt(d) : 1.0;
+    }
+}
+// y = S x (inv = 0) or y = x / S (inv = 1); y may alias x
+__global__ void adj_scale_kernel(long long n, const double* S, const double* x, double* y, int inv)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = inv ? x[i] / S[i] : x[i] * S[i];
 }
 
 // y = J_cons^T x (free dofs)
@@ -304,7 +325,8 @@ extern "C" int gm_set_friction(gm_ctx* c, const double* f, int64_t n)
     return GM_OK;
 }
 
-// FGMRES solve of J_cons^T x = b (b in adj_b, x in adj_x).
+// FGMRES solve of J_cons^T x = b (b in adj_b, x in adj_x), run on the scaled
+// system (S J^T S) y = S b, x = S y.
 static int adj_solve(gm_ctx* c, double rtol, int maxit, gm_solve_report* rep, cudaStream_t s)
 {
     const long long N = c->N, n4 = 4 * N;
@@ -314,8 +336,33 @@ static int adj_solve(gm_ctx* c, double rtol, int maxit, gm_solve_report* rep, cu
     double* w = c->adj_w.as<double>();
     double* b = c->adj_b.as<double>();
     double* x = c->adj_x.as<double>();
+    double* S = c->adj_s.as<double>();
+    double* u = c->adj_u.as<double>();
     int rc;
     if ((rc = gm_launch_block_jacobi(c, s))) return rc;   // symmetric Newton tangent of the frozen state
+    adj_make_scale_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(N, c->ddiagK.as<double>(), c->ddiagA.as<double>(), S);
+    GM_LAUNCHED(c);
+    adj_scale_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(n4, S, b, b, 0);
+    GM_LAUNCHED(c);
+    // scaled operator and preconditioner
+    auto op = [&](const double* v, double* y) -> int {
+        adj_scale_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(n4, S, v, u, 0);
+        GM_LAUNCHED(c);
+        int e = apply_adjoint_operator(c, u, y, s);
+        if (e) return e;
+        adj_scale_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(n4, S, y, y, 0);
+        GM_LAUNCHED(c);
+        return GM_OK;
+    };
+    auto prec = [&](const double* v, double* z, double prt, long long* ikp) -> int {
+        adj_scale_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(n4, S, v, u, 1);
+        GM_LAUNCHED(c);
+        int e = apply_preconditioner(c, u, z, prt, 500, s, ikp);
+        if (e) return e;
+        adj_scale_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(n4, S, z, z, 1);
+        GM_LAUNCHED(c);
+        return GM_OK;
+    };
     GM_CUDA_TRY(c, cudaMemsetAsync(x, 0, n4 * sizeof(double), s));
     double beta0;
     if ((rc = dot(c, n4, b, b, &beta0, s))) return rc;
@@ -327,7 +374,7 @@ static int adj_solve(gm_ctx* c, double rtol, int maxit, gm_solve_report* rep, cu
     // flexible GMRES(m), right preconditioned; restart from r = b - A x
     while (beta0 > 0 && res > rtol * beta0 && it < maxit) {
         double* r = V;   // V[0]
-        if ((rc = apply_adjoint_operator(c, x, w, s))) return rc;
+        if ((rc = op(x, w))) return rc;
         GM_CUDA_TRY(c, cudaMemcpyAsync(r, b, n4 * 8, cudaMemcpyDeviceToDevice, s));
         if ((rc = gm_launch_axpby(c, n4, -1.0, w, 1.0, r, s))) return rc;
         double beta;
@@ -342,8 +389,8 @@ static int adj_solve(gm_ctx* c, double rtol, int maxit, gm_solve_report* rep, cu
         for (j = 0; j < m && it < maxit; ++j, ++it) {
             double* vj = V + (size_t)j * n4;
             double* zj = Z + (size_t)j * n4;
-            if ((rc = apply_preconditioner(c, vj, zj, prtol, 500, s, &ik))) return rc;
-            if ((rc = apply_adjoint_operator(c, zj, w, s))) return rc;
+            if ((rc = prec(vj, zj, prtol, &ik))) return rc;
+            if ((rc = op(zj, w))) return rc;
             for (int i = 0; i <= j; ++i) {
                 double h;
                 if ((rc = dot(c, n4, w, V + (size_t)i * n4, &h, s))) return rc;
@@ -383,12 +430,14 @@ static int adj_solve(gm_ctx* c, double rtol, int maxit, gm_solve_report* rep, cu
         for (int i = 0; i < j; ++i)
             if ((rc = gm_launch_axpby(c, n4, y[i], Z + (size_t)i * n4, 1.0, x, s))) return rc;
     }
-    // true residual
-    if ((rc = apply_adjoint_operator(c, x, w, s))) return rc;
+    // true residual (scaled), then x = S y
+    if ((rc = op(x, w))) return rc;
     if ((rc = gm_launch_axpby(c, n4, 1.0, b, -1.0, w, s))) return rc;
     double rfin;
     if ((rc = dot(c, n4, w, w, &rfin, s))) return rc;
     rfin = std::sqrt(rfin);
+    adj_scale_kernel<<<GM_RED_BLOCKS, 256, 0, s>>>(n4, S, x, x, 0);
+    GM_LAUNCHED(c);
     if (rep) {
         rep->iterations = it;
         rep->rel_residual = beta0 > 0 ? rfin / beta0 : 0.0;

@@ -284,6 +284,7 @@ struct gm_ctx {
     int fault_cons = 0;                                // tangent variant used by the fault kernel
     double Lref[64] = {};                              // nodal L of the reference cell (k/mu = 1)
     DevBuf adj_V, adj_Z, adj_w, adj_b, adj_x, adj_t;   // adjoint (FGMRES) work, allocated on first use
+    DevBuf adj_s, adj_u;                               // row scaling of the adjoint system, scratch
     int adj_m = 0;
     int adj_prec = 0;            // preconditioner precision (GM_F64 / GM_F32)
     double adj_prtol = 1e-8;     // preconditioner tolerance

@@ -191,3 +191,72 @@ def test_multistep_adjoint_matches_oracle_and_fd():
     fd = (Js[0] - Js[1]) / (2 * h)
     assert pred == pytest.approx(fd, rel=1e-5)
 
+
+
+def test_aquifer_caprock_pressure_gradient():
+    """Gradient of the caprock pressure (hanging-wall nodes 1000-1200 m high)
+    after three steps of the small faulted-aquifer case (layers over six
+    decades of permeability, per-pair in-situ tractions, sheared grid, a
+    slipping pair), checkpoints every 2 steps: equal to the oracle's
+    multi-step adjoint, and to central differences of GPU runs along log Q and
+    a random log-permeability direction (1e-5).  The friction derivative is
+    much smaller than the source derivative here, so its difference quotient
+    carries the noise of the Newton tolerance (1e-10, the FP64 floor of this
+    case): checked to 1e-4."""
+    need_gpu()
+    import paper_2410_17133_gb300 as gm
+    from oracle import adjoint as oadj
+    prob = W.faulted_aquifer(nv=20, ny=6, nz=8, steps=3, Q=0.5)
+    K = 3
+    nb = (prob.nx + 1) * (prob.ny + 1)
+    node = np.arange(prob.n_nodes)
+    height = (node % (prob.nx + 1)) * prob.h[0]
+    cap = np.where((height >= 1000) & (height <= 1200) & (node // nb < prob.kf))[0]
+    kw = {"newton_rtol": 1e-10}
+    g_p = np.zeros(prob.n_nodes)
+    g_p[cap] = 1.0 / P0
+
+    def objective_grad(st):
+        return None, cuda(g_p), None
+
+    s = solver_for(prob)
+    final, gk, gf, gq = gm.run_with_adjoint(s, prob.dts[:K], objective_grad, checkpoint_every=2,
+                                            step_kw=kw, rtol=1e-11)
+    assert (final["flags"] == 2).sum() >= 1
+    model = fem.Model(prob)
+    st = osolve.initial_state(model)
+    traj = []
+    for dt in prob.dts[:K]:
+        h_prev = st.dlie.copy()
+        osolve.implicit_step(model, st, dt, rtol=1e-10)
+        traj.append(dict(u=st.u.copy(), p=st.p.copy(), h_prev=h_prev))
+    go = oadj.adjoint_multistep(model, traj, prob.dts[:K], dJ_dp=g_p)
+    assert rel(gk.cpu().numpy(), go["g_logk"]) < 1e-6
+    assert rel(gf.cpu().numpy(), go["g_f"]) < 1e-6
+    assert gq == pytest.approx(go["g_logQ"], rel=1e-6)
+
+    k0 = np.asarray(prob.k, float)
+    vk = np.random.default_rng(12).normal(size=k0.size)
+
+    def J(k=None, f=None, qs=1.0):
+        s2 = solver_for(prob)
+        if k is not None:
+            s2.set_permeability(k)
+        if f is not None:
+            s2.set_friction(np.array([f]))
+        if qs != 1.0:
+            s2.loads(prob.fu, prob.fp * qs)
+        for dt in prob.dts[:K]:
+            s2.step(dt, **kw)
+        stt = s2.get_state()
+        assert np.array_equal(stt["flags"], final["flags"])
+        return float(np.sum(stt["p"][cap]) / P0)
+
+    h = 1e-4
+    fd_q = (J(qs=math.exp(h)) - J(qs=math.exp(-h))) / (2 * h)
+    assert gq == pytest.approx(fd_q, rel=1e-5)
+    h = 1e-3
+    fd_k = (J(k=k0 * np.exp(h * vk)) - J(k=k0 * np.exp(-h * vk))) / (2 * h)
+    assert float(gk.cpu().numpy() @ vk) == pytest.approx(fd_k, rel=1e-5)
+    fd_f = (J(f=prob.fault.f + h) - J(f=prob.fault.f - h)) / (2 * h)
+    assert float(gf.sum().item()) == pytest.approx(fd_f, rel=1e-4)
