@@ -407,7 +407,6 @@ int gm_launch_axpy_scaled_f2d(gm_ctx* c, long long n, const double* sc, const fl
 // Deterministic dot products: out[0] = x.y (and out[1] = x2.y2 if x2) as doubles
 int gm_launch_dot(gm_ctx* c, long long n, const double* x, const double* y, const double* x2,
                   const double* y2, double* out, cudaStream_t s);
-int gm_launch_jacobi_apply(gm_ctx* c, int which, const double* r, double* z, cudaStream_t s);
 
 // Solvers (gm_solve.cu)
 // x_zero: the initial guess is zero (x is overwritten), which skips the

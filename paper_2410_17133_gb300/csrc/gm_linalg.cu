@@ -401,31 +401,6 @@ int gm_launch_dot(gm_ctx* c, long long n, const double* x, const double* y, cons
     return GM_OK;
 }
 
-// z = M^-1 r (outer-loop preconditioner application, FP64)
-template <int WHICH>
-__global__ void gm_jacobi_apply_kernel(long long N, const double* mi, const double* r, double* z)
-{
-    constexpr int NC = Prec<double, WHICH>::NC;
-    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x) {
-        double rr[NC], zz[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) rr[c] = r[c * N + n];
-        Prec<double, WHICH>::apply(mi, N, n, rr, zz);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) z[c * N + n] = zz[c];
-    }
-}
-
-int gm_launch_jacobi_apply(gm_ctx* c, int which, const double* r, double* z, cudaStream_t s)
-{
-    if (which == 0)
-        gm_jacobi_apply_kernel<0><<<GM_RED_BLOCKS, 256, 0, s>>>(c->N, c->dKinv64.as<double>(), r, z);
-    else
-        gm_jacobi_apply_kernel<1><<<GM_RED_BLOCKS, 256, 0, s>>>(c->N, c->dAinv64.as<double>(), r, z);
-    GM_LAUNCHED(c);
-    return GM_OK;
-}
 
 // ---------------------------------------------------------------------------
 // PCG steps around the multigrid preconditioner (FP32 K_T solves): the update
