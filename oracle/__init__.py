@@ -19,7 +19,11 @@ Fluid-induced Fault Slip in Poroelastic Media") defines:
                schur_system).
   analytic.py  closed forms used to pin the oracle: 1-D consolidation series,
                the line-source (Theis) fault pressure, the circular slip-front
-               amplification lambda(T) (Sec. 4.2).
+               amplification lambda(T) (Sec. 4.2), Cryer's centre pressure
+               (Sec. 4.1).
+  tet.py       the paper's own discretisation without faults: P1 tetrahedra
+               for displacement and pressure (Sec. 3.1), assembly and the
+               backward-Euler monolithic step (Cryer's sphere, Sec. 4.1).
   rows.py      the same operators evaluated one node at a time, for sampled
                checks on meshes too large to assemble.
 

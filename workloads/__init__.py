@@ -19,7 +19,8 @@ Vectors are stored field-major ("SoA"): u as (3, N), p as (N,).
 
 The workloads restate the paper's verification and application set-ups
 (Sec. 4.2 injection-induced slip, Table 1; Sec. 5 faulted aquifer) on
-structured grids; the paper's own meshes and datasets are not used.
+structured grids, and Cryer's sphere (Sec. 4.1) on a generated tetrahedral
+mesh of one octant; the paper's own meshes and datasets are not used.
 """
 from __future__ import annotations
 
@@ -40,6 +41,8 @@ __all__ = [
     "adjoint_lognormal",
     "adjoint_objective",
     "faulted_aquifer",
+    "TetProblem",
+    "cryer_octant",
     "column_terzaghi",
     "theis_plate",
     "tiny_faulted",
@@ -344,6 +347,95 @@ def faulted_aquifer(nv: int = 128, ny: int = 256, nz: int = 256, steps: int = 10
                    h=(hx, hy, hz), shear=(sx, 0.0), kf=kf, fault=fault, E=E, k=k, nu=0.15,
                    alpha=0.64, M=22.7e9, mu_f=0.89e-3, fixed=fixed, fu=fu, fp=fp,
                    dts=[dt] * steps, notes=f"seed={seed} dip={dip_deg} throw={throw}")
+
+
+@dataclasses.dataclass
+class TetProblem:
+    """An unstructured P1-tetrahedron problem without fault."""
+
+    name: str
+    nodes: np.ndarray       # (N, 3) coordinates [m]
+    tets: np.ndarray        # (M, 4) vertex ids, positive orientation
+    E: float
+    nu: float
+    alpha: float
+    M: float
+    k: float
+    mu_f: float
+    fixed: np.ndarray       # uint8 (4, N): 1 = homogeneous Dirichlet on (ux, uy, uz, p)
+    load_tris: np.ndarray   # (T, 3) surface triangles carrying the normal traction, outward order
+    sigma0: float           # compressive normal traction on load_tris [Pa]
+    dts: list
+    notes: str = ""
+
+
+def cryer_octant(n: int = 8, R: float = 1.0, sigma0: float = 1e6, steps: int = 40,
+                 E: float = 20e9, nu: float = 0.25, alpha: float = 0.8, M: float = 50e9,
+                 k: float = 1e-15, mu_f: float = 1e-3) -> TetProblem:
+    """Cryer's sphere (Sec. 4.1) as one octant of a ball of radius R.
+
+    The unit cube [0, 1]^3 with n cells per edge is mapped onto the octant by
+    x -> R x |x|_inf / |x|_2, so its faces x_i = 1 land on the sphere and its
+    faces x_i = 0 on the symmetry planes; each cell is cut into the 6 Kuhn
+    tetrahedra along its main diagonal (conforming between cells).  Symmetry
+    planes: normal displacement 0; sphere: p = 0 and a compressive normal
+    traction sigma0.  Time steps: a short first step (the undrained response)
+    then a geometric series up to t* = c t / R^2 = 1 with c the consolidation
+    coefficient (k/mu) / (1/M + alpha^2 / K_v)."""
+    g = np.linspace(0.0, 1.0, n + 1)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    P = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    ninf = np.max(np.abs(P), axis=1)
+    n2 = np.linalg.norm(P, axis=1)
+    scale = np.where(n2 > 0, ninf / np.where(n2 > 0, n2, 1.0), 0.0)
+    nodes = R * P * scale[:, None]
+    idx = lambda i, j, kk: (i * (n + 1) + j) * (n + 1) + kk
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    tets = []
+    for i in range(n):
+        for j in range(n):
+            for kk in range(n):
+                for pm in perms:
+                    v = [0, 0, 0]
+                    path = [idx(i, j, kk)]
+                    for ax in pm:
+                        v[ax] += 1
+                        path.append(idx(i + v[0], j + v[1], kk + v[2]))
+                    tets.append(path)
+    tets = np.array(tets)
+    a, b, c, d = (nodes[tets[:, q]] for q in range(4))
+    vol = np.einsum("ij,ij->i", np.cross(b - a, c - a), d - a)
+    swap = vol < 0
+    tets[swap, 1], tets[swap, 2] = tets[swap, 2].copy(), tets[swap, 1].copy()
+    N = nodes.shape[0]
+    fixed = np.zeros((4, N), np.uint8)
+    for ax in range(3):
+        fixed[ax, P[:, ax] == 0.0] = 1
+    on_sphere = ninf == 1.0
+    fixed[3, on_sphere] = 1
+    # surface triangles: tetrahedron faces with all three vertices on one cube face x_i = 1
+    tris = []
+    faces = [(0, 1, 2, 3), (0, 1, 3, 2), (0, 2, 3, 1), (1, 2, 3, 0)]
+    for t in tets:
+        for f0, f1, f2, opp in faces:
+            tri = [t[f0], t[f1], t[f2]]
+            if any(np.all(P[tri, ax] == 1.0) for ax in range(3)):
+                x0, x1, x2 = nodes[tri]
+                nrm = np.cross(x1 - x0, x2 - x0)
+                if np.dot(nrm, x0 - nodes[t[opp]]) < 0:
+                    tri = [tri[0], tri[2], tri[1]]
+                tris.append(tri)
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    Kv = lam + E / (1 + nu)
+    c = (k / mu_f) / (1.0 / M + alpha * alpha / Kv)
+    t_end = R * R / c
+    t0 = 1e-4 * t_end
+    growth = (t_end / t0) ** (1.0 / (steps - 1))
+    times = [t0 * growth ** s for s in range(steps)]
+    dts = [times[0]] + [times[s] - times[s - 1] for s in range(1, steps)]
+    return TetProblem(name=f"cryer{n}", nodes=nodes, tets=tets, E=E, nu=nu, alpha=alpha, M=M, k=k,
+                      mu_f=mu_f, fixed=fixed, load_tris=np.array(tris), sigma0=sigma0, dts=dts,
+                      notes="octant of a ball; Kuhn tetrahedra")
 
 
 def column_terzaghi(nz: int = 16, H: float = 1.0, load: float = 1e6, steps: int = 200,
