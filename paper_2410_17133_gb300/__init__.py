@@ -17,7 +17,7 @@ import numpy as np
 
 from ._build import LIB
 
-__all__ = ["lib", "GMError", "Solver", "OP", "OPEN", "STICK", "SLIP", "load_library"]
+__all__ = ["lib", "GMError", "Solver", "TetSolver", "OP", "OPEN", "STICK", "SLIP", "load_library"]
 
 OP = {"KB": 0, "KT": 1, "A22": 2, "APU": 3, "AUP": 4, "J": 5}
 OPEN, STICK, SLIP = 0, 1, 2
@@ -91,6 +91,13 @@ _SIG = {
                                   C.POINTER(SolveReport), _P]),
     "gm_set_adjoint_options": (C.c_int, [_P, C.c_int, C.c_double, C.c_int]),
     "gm_set_insitu": (C.c_int, [_P, _P, _P, C.c_int64]),
+    "gm_tet_create": (C.c_int, [C.POINTER(_P), C.c_int]),
+    "gm_tet_destroy": (C.c_int, [_P]),
+    "gm_tet_last_error": (C.c_char_p, [_P]),
+    "gm_tet_mesh": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64]),
+    "gm_tet_materials": (C.c_int, [_P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                   C.c_double]),
+    "gm_tet_apply": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int, _P]),
     "gm_set_preconditioner": (C.c_int, [_P, C.c_int]),
     "gm_adjoint_sweep_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _D,
                                         C.c_double, C.c_int, C.POINTER(SolveReport), _P]),
@@ -443,6 +450,68 @@ def implicit_step_fn():
                     None, None, None, None)
 
     return ImplicitStep
+
+
+class TetSolver:
+    """Operators of P1 tetrahedra on an unstructured mesh (include/gm_tet.h):
+    argument marshalling only."""
+
+    def __init__(self, device: int = 0):
+        self._L = load_library()
+        h = _P()
+        rc = self._L.gm_tet_create(C.byref(h), int(device))
+        if rc != 0:
+            raise GMError(rc, "gm_tet_create failed")
+        self.h = h
+        self.device = device
+        self.N = self.M = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.gm_tet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, rc):
+        if rc != 0:
+            msg = self._L.gm_tet_last_error(self.h)
+            raise GMError(rc, msg.decode() if msg else "")
+
+    def mesh(self, nodes, tets):
+        x = np.ascontiguousarray(nodes, np.float64).reshape(-1)
+        t = np.ascontiguousarray(tets, np.int64).reshape(-1)
+        self._chk(self._L.gm_tet_mesh(self.h, _dptr(x), x.size // 3,
+                                      t.ctypes.data_as(C.c_void_p), t.size // 4))
+        self.N, self.M = x.size // 3, t.size // 4
+
+    def materials(self, E, nu, alpha, M, k, mu_f):
+        self._chk(self._L.gm_tet_materials(self.h, float(E), float(nu), float(alpha), float(M), float(k),
+                                           float(mu_f)))
+
+    @classmethod
+    def from_problem(cls, prob, device: int = 0):
+        s = cls(device)
+        s.mesh(prob.nodes, prob.tets)
+        s.materials(prob.E, prob.nu, prob.alpha, prob.M, prob.k, prob.mu_f)
+        return s
+
+    def apply(self, which, x, dt=0.0, y=None, stream=None):
+        """y = A x for which in ('KB', 'APU', 'AUP', 'A22', 'J'); x, y CUDA tensors."""
+        import torch
+        w = OP[which] if isinstance(which, str) else int(which)
+        shape_out = {0: (3, self.N), 1: (3, self.N), 2: (self.N,), 3: (3, self.N), 4: (self.N,),
+                     5: (4, self.N)}[w]
+        if y is None:
+            y = torch.empty(shape_out, dtype=x.dtype, device=x.device)
+        dt_code = F64 if x.dtype == torch.float64 else F32
+        assert x.is_contiguous() and y.is_contiguous() and y.dtype == x.dtype
+        self._chk(self._L.gm_tet_apply(self.h, w, _tptr(x), _tptr(y), float(dt), dt_code, _stream_ptr(stream)))
+        return y
 
 
 def run_with_adjoint(solver, dts, objective_grad, checkpoint_every=5, step_kw=None, rtol=1e-10, maxit=300):

@@ -13,7 +13,7 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libgm.so")
 SOURCES = ["gm_apply_f64.cu", "gm_apply_f32.cu", "gm_fault.cu", "gm_linalg.cu", "gm_solve.cu",
-           "gm_host.cu", "gm_noalloc.cu", "gm_adjoint.cu", "gm_mg.cu"]
+           "gm_host.cu", "gm_noalloc.cu", "gm_adjoint.cu", "gm_mg.cu", "gm_tet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -39,7 +39,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    headers.append(os.path.join(HERE, "..", "include", "gm.h"))
+    inc = os.path.join(HERE, "..", "include")
+    headers += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     cc = nvcc()
     jobs = []
     objs = []

@@ -1,5 +1,5 @@
 """The C-ABI library builds for sm_103a, loads, and exports every entry point
-that include/gm.h declares (no GPU needed; no compute calls)."""
+that the headers in include/ declare (no GPU needed; no compute calls)."""
 import ctypes
 import os
 import re
@@ -8,7 +8,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_symbols():
-    src = open(os.path.join(ROOT, "include", "gm.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "\n".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(gm_\w+)\s*\(", src, flags=re.M)))
 
