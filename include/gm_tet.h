@@ -51,6 +51,28 @@ int gm_tet_materials(gm_tet* t, double E, double nu, double alpha, double M, dou
 int gm_tet_apply(gm_tet* t, int which, const void* x_dev, void* y_dev, double dt, int dtype,
                  void* stream);
 
+/* Dirichlet constraints for gm_tet_step: 4*N bytes, fixed[c*N + n] = 1 sets
+ * component c (ux, uy, uz, p) of node n to zero (homogeneous). */
+int gm_tet_dirichlet(gm_tet* t, const uint8_t* fixed_host, int64_t n);
+
+/* Nodal forces of a compressive normal traction sigma0 on surface triangles
+ * (3*n_tris vertex ids; the vertex order gives the outward side by the right-
+ * hand rule): -sigma0 (A/3) n at each vertex of each triangle, replacing the
+ * previous forces.  Used by gm_tet_step. */
+int gm_tet_surface_load(gm_tet* t, const int64_t* tris_host, int64_t n_tris, double sigma0);
+
+/* One backward-Euler step of the fault-free poroelastic problem (Sec. 3.3):
+ * K u - A p = f,  A^T (u - u_n) + S (p - p_n) + dt C p = 0, with the
+ * Dirichlet constraints and loads above.  u_dev (3N) and p_dev (N) hold the
+ * previous state on entry and the new one on return (constrained entries 0).
+ * Solved by Prevost's partitioned CG (Sec. 3.3.2): CG on the Schur complement
+ * (S + dt C) + A^T K^-1 A, preconditioned by the diagonal of S + dt C,
+ * relative tolerance rtol; inner K solves by PCG with 3x3 nodal block Jacobi
+ * to rtol/100.  FP64.  report: outer iterations and final relative residual.
+ * GM_ENOCONV if an iteration limit (maxit) is reached.  Synchronises. */
+int gm_tet_step(gm_tet* t, double dt, double* u_dev, double* p_dev, double rtol, int maxit,
+                gm_solve_report* report_host, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -98,6 +98,9 @@ _SIG = {
     "gm_tet_materials": (C.c_int, [_P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                                    C.c_double]),
     "gm_tet_apply": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int, _P]),
+    "gm_tet_dirichlet": (C.c_int, [_P, C.POINTER(C.c_uint8), C.c_int64]),
+    "gm_tet_surface_load": (C.c_int, [_P, _P, C.c_int64, C.c_double]),
+    "gm_tet_step": (C.c_int, [_P, C.c_double, _P, _P, C.c_double, C.c_int, C.POINTER(SolveReport), _P]),
     "gm_set_preconditioner": (C.c_int, [_P, C.c_int]),
     "gm_adjoint_sweep_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _D,
                                         C.c_double, C.c_int, C.POINTER(SolveReport), _P]),
@@ -493,11 +496,32 @@ class TetSolver:
         self._chk(self._L.gm_tet_materials(self.h, float(E), float(nu), float(alpha), float(M), float(k),
                                            float(mu_f)))
 
+    def dirichlet(self, fixed):
+        f = np.ascontiguousarray(fixed, np.uint8).reshape(-1)
+        self._chk(self._L.gm_tet_dirichlet(self.h, f.ctypes.data_as(C.POINTER(C.c_uint8)), f.size))
+
+    def surface_load(self, tris, sigma0):
+        t = np.ascontiguousarray(tris, np.int64).reshape(-1)
+        self._chk(self._L.gm_tet_surface_load(self.h, t.ctypes.data_as(C.c_void_p), t.size // 3, float(sigma0)))
+
+    def step(self, dt, u, p, rtol=1e-12, maxit=5000, stream=None):
+        """gm_tet_step: u (3, N), p (N,) float64 CUDA tensors updated in place."""
+        rep = SolveReport()
+        self._chk(self._L.gm_tet_step(self.h, float(dt), _tptr(u), _tptr(p), rtol, maxit, C.byref(rep),
+                                      _stream_ptr(stream)))
+        return dict(iterations=rep.iterations, rel_residual=rep.rel_residual)
+
     @classmethod
     def from_problem(cls, prob, device: int = 0):
+        """Mesh and materials; for a problem with loads (workloads.TetProblem)
+        also its Dirichlet constraints and surface traction."""
         s = cls(device)
         s.mesh(prob.nodes, prob.tets)
         s.materials(prob.E, prob.nu, prob.alpha, prob.M, prob.k, prob.mu_f)
+        if getattr(prob, "fixed", None) is not None:
+            s.dirichlet(prob.fixed)
+        if getattr(prob, "load_tris", None) is not None:
+            s.surface_load(prob.load_tris, prob.sigma0)
         return s
 
     def apply(self, which, x, dt=0.0, y=None, stream=None):

@@ -53,3 +53,32 @@ def test_tet_apply_is_repeatable(case):
     a = s.apply("KB", x).cpu().numpy()
     b = s.apply("KB", x).cpu().numpy()
     assert np.array_equal(a, b)
+
+
+def test_tet_steps_match_oracle_cryer():
+    """Cryer's sphere on the GPU (octant, 6 cells per radius, the first 20
+    steps of the geometric schedule): each step by the library's partitioned
+    CG (gm_tet_step) equals the oracle's direct solve of the monolithic system
+    within 1e-9 in u and p, and the centre pressure shows the undrained start
+    and the Mandel-Cryer rise."""
+    need_gpu()
+    import paper_2410_17133_gb300 as gm
+    prob = W.cryer_octant(n=6, steps=40)
+    K = 20
+    m, ts, pc, u_ref, p_ref = tet.run(prob, nsteps=K)
+    s = gm.TetSolver.from_problem(prob)
+    u = torch.zeros((3, m.N), dtype=torch.float64, device="cuda")
+    p = torch.zeros(m.N, dtype=torch.float64, device="cuda")
+    mu_, mp_ = np.zeros(3 * m.N), np.zeros(m.N)
+    centre = int(np.argmin(np.linalg.norm(prob.nodes, axis=1)))
+    pg = []
+    for k in range(K):
+        s.step(prob.dts[k], u, p, rtol=1e-12)
+        mu_, mp_ = m.step(mu_, mp_, prob.dts[k])
+        assert rel(u.cpu().numpy().reshape(-1), mu_) < 1e-9, k
+        assert rel(p.cpu().numpy(), mp_) < 1e-9, k
+        pg.append(p[centre].item())
+    assert np.allclose(pg, pc, rtol=1e-9)
+    from oracle import analytic as A
+    prm = A.cryer_params(prob.E, prob.nu, prob.alpha, prob.M, prob.k, prob.mu_f, prob.sigma0)
+    assert 0.85 < pg[0] / prm["p0"] < 1.1 and max(pg) / prm["p0"] > 1.05
