@@ -70,3 +70,68 @@ def test_cryer_octant_centre_pressure():
     assert np.max(np.abs(num - an)) / an.max() < 0.04
     assert num[0] == pytest.approx(an[0], rel=0.02)
     assert num.max() > 1.1 and num[-1] < 0.05
+
+
+def test_tet_element_energy_and_storage_quadrature():
+    """Values, not only structure: the strain energy of a linear displacement
+    equals V (lambda tr(eps)^2 + 2 mu eps:eps) with eps = sym(H) (isotropic
+    Hooke's law, Sec. 2.1), and the storage energy of a linear pressure equals
+    (1/M) times its square integrated by the degree-2 exact four-point rule on
+    the tetrahedron (Keast), which shares nothing with the closed-form matrix."""
+    X = random_tet(7)
+    Ke, _, Me, _ = (m[0] for m in tet.tet_element_matrices(X[None], E, NU, ALPHA, 1.0 / M, K / MU))
+    _, V = tet.tet_gradients(X[None])
+    V = V[0]
+    lam = E * NU / ((1 + NU) * (1 - 2 * NU))
+    mu = E / (2 * (1 + NU))
+    H = np.random.default_rng(8).normal(size=(3, 3))
+    eps = 0.5 * (H + H.T)
+    u = (X @ H.T).reshape(-1)
+    assert u @ Ke @ u == pytest.approx(V * (lam * np.trace(eps) ** 2 + 2 * mu * np.sum(eps * eps)),
+                                       rel=1e-11)
+    a, b = 0.5854101966249685, 0.1381966011250105
+    p = np.random.default_rng(9).normal(size=4)
+    quad = 0.0
+    for q in range(4):
+        bary = np.full(4, b)
+        bary[q] = a
+        quad += V / 4 * (bary @ p) ** 2
+    assert p @ Me @ p == pytest.approx(quad / M, rel=1e-12)
+
+
+def test_tet_assembled_patch_identities():
+    """Assembly on the Cryer octant (4 cells per radius, curved surface):
+    a linear displacement leaves no force at nodes off the boundary (constant
+    stress is divergence free), a linear pressure leaves no Darcy flux there,
+    A_pu^T of a linear displacement is alpha tr(H) times each node's lumped
+    volume, the storage rows sum to that volume / M, and the surface load's
+    resultant is -sigma0 times the area that the mesh's symmetry face
+    x = 0 covers (the closed polyhedral surface has zero net area vector)."""
+    prob = W.cryer_octant(4, steps=2)
+    m = tet.TetModel(prob)
+    x = prob.nodes
+    tol = 1e-9
+    interior = ((x > tol).all(axis=1)) & (np.linalg.norm(x, axis=1) < 1.0 - 1e-3)
+    interior &= ~np.isin(np.arange(m.N), prob.load_tris.reshape(-1))
+    assert interior.sum() >= 8
+    H = np.random.default_rng(10).normal(size=(3, 3))
+    u = (x @ H.T).T.reshape(-1)                                   # field-major
+    f = (m.Kb @ u).reshape(3, m.N)
+    scale = np.abs(m.Kb).max() * np.abs(u).max()
+    assert np.abs(f[:, interior]).max() < 1e-11 * scale
+    g = np.array([0.4, -0.9, 1.3])
+    p = x @ g
+    assert np.abs((m.C @ p)[interior]).max() < 1e-11 * np.abs(m.C).max() * np.abs(p).max()
+    _, V = tet.tet_gradients(x[prob.tets])
+    vol = np.zeros(m.N)
+    np.add.at(vol, prob.tets, np.repeat(V[:, None] / 4, 4, axis=1))
+    assert np.allclose(m.Apu.T @ u, ALPHA * np.trace(H) * vol, rtol=1e-11, atol=0)
+    assert np.allclose(np.asarray(m.S.sum(axis=1)).ravel(), vol / M, rtol=1e-12)
+    faces = np.concatenate([prob.tets[:, [0, 1, 2]], prob.tets[:, [0, 1, 3]], prob.tets[:, [0, 2, 3]],
+                            prob.tets[:, [1, 2, 3]]])
+    on_x0 = faces[(x[faces, 0] == 0.0).all(axis=1)]
+    a = x[on_x0]
+    area_x0 = 0.5 * np.linalg.norm(np.cross(a[:, 1] - a[:, 0], a[:, 2] - a[:, 0]), axis=1).sum()
+    fx = m.fu.reshape(3, m.N)[0].sum()
+    assert fx == pytest.approx(-prob.sigma0 * area_x0, rel=1e-12)
+    assert area_x0 == pytest.approx(np.pi / 4, rel=0.05)          # quarter disc of radius 1
