@@ -24,6 +24,9 @@ Fluid-induced Fault Slip in Poroelastic Media") defines:
   tet.py       the paper's own discretisation without faults: P1 tetrahedra
                for displacement and pressure (Sec. 3.1), assembly and the
                backward-Euler monolithic step (Cryer's sphere, Sec. 4.1).
+  tetfault.py  P1 tetrahedra with a fault: interface elements on the fault
+               triangles (Sec. 3.1.1-3.1.2), nodal quadrature per pair, the
+               triangle Laplacian; stepped by solve.py's Newton unchanged.
   rows.py      the same operators evaluated one node at a time, for sampled
                checks on meshes too large to assemble.
 

@@ -57,10 +57,13 @@ def tet_B(G):
 
 
 def tet_element_matrices(X, E, nu, alpha, invM, cond):
-    """K (ne,12,12), A (ne,12,4), Ms (ne,4,4), L (ne,4,4) for P1 tetrahedra."""
+    """K (ne,12,12), A (ne,12,4), Ms (ne,4,4), L (ne,4,4) for P1 tetrahedra;
+    E and cond (= k / mu) scalar or one per element."""
     G, V = tet_gradients(X)
     B = tet_B(G)
-    D = elasticity_D(np.full(X.shape[0], E), nu)
+    ne = X.shape[0]
+    D = elasticity_D(np.broadcast_to(np.asarray(E, float), (ne,)).copy(), nu)
+    cond = np.broadcast_to(np.asarray(cond, float), (ne,))[:, None, None]
     K = V[:, None, None] * np.einsum("eia,eij,ejb->eab", B, D, B)
     Bm = np.einsum("eia,i->ea", B, VOIGT_M)
     A = alpha * (V / 4.0)[:, None, None] * Bm[:, :, None] * np.ones(4)[None, None, :]

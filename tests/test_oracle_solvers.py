@@ -5,6 +5,7 @@ reproduces 1-D consolidation and the line-source fault pressure."""
 import math
 
 import numpy as np
+from scipy import special
 import pytest
 
 import workloads as W
@@ -81,22 +82,43 @@ def test_terzaghi_consolidation_converges_at_second_order():
     assert e8 / e16 > 2.5
 
 
+def pressure_front(xy, p_rel):
+    """Radius where the fault pressure falls to dp* E1(1) along the +x and +y
+    rays through the source (linear interpolation between nodes)."""
+    level = special.exp1(1.0)
+    out = []
+    for ax in (0, 1):
+        ray = (np.abs(xy[:, 1 - ax]) < 1e-9) & (xy[:, ax] > 0)
+        o = np.argsort(xy[ray, ax])
+        rr, pp = xy[ray, ax][o], p_rel[ray][o]
+        k = np.nonzero(pp < level)[0][0]
+        out.append(rr[k - 1] + (pp[k - 1] - level) / (pp[k - 1] - pp[k]) * (rr[k] - rr[k - 1]))
+    return np.array(out)
+
+
 def test_theis_fault_pressure():
-    """Impermeable, uncoupled matrix: fault pressure vs dp* E1(r^2/4Dt) at radii
-    3..8 cells, while the front stays far from the box edge (Sec. 4.2)."""
-    prob = W.theis_plate(n=32, steps=30)
+    """Impermeable, uncoupled matrix (Sec. 4.2): after 50 steps (t = 3600 s)
+    the pressure front, where p = dp* E1(1), lies within the paper's 8 % of
+    L = sqrt(4Dt) (4.6 cells here) on both grid axes, and the pressure at
+    radii of 3 to 8 cells, where it spans 0.01 to 0.65 dp*, is within 6 % of
+    dp* of dp* E1(r^2/4Dt) (the log-singular point source on 1.25 m cells
+    costs 5 % at 3 cells)."""
+    prob = W.theis_plate(n=32, steps=50)
     model, res = solve.run(prob)
     fp = prob.fault
     t = sum(prob.dts)
     X = model.mesh.coords()
     pairs = model.fg["pairs"]
     Q = prob.fp.sum()
+    dps = analytic.theis_dpstar(Q, prob.mu_f, fp.wk_par)
     r = np.linalg.norm(X[pairs[:, 0], :2], axis=1)
     p = res[-1].p[pairs[:, 0]]
     D = analytic.fault_diffusivity(fp.wk_par, fp.MF, prob.mu_f, fp.w0)
-    assert math.sqrt(4 * D * t) < 10.0                   # front well inside 20 m
+    L = math.sqrt(4 * D * t)
+    assert 4 * prob.h[0] < L < 10.0                     # resolved, and well inside 20 m
+    assert np.abs(pressure_front(X[pairs[:, 0], :2], p / dps) / L - 1).max() < 0.08
     h = prob.h[0]
     sel = (r >= 3 * h - 1e-9) & (r <= 8 * h + 1e-9)
     pan = analytic.theis_pressure(r[sel], t, Q, prob.mu_f, fp.wk_par, fp.MF, fp.w0)
-    err = np.abs(p[sel] - pan) / analytic.theis_dpstar(Q, prob.mu_f, fp.wk_par)
-    assert err.max() < 0.05
+    assert pan.max() > 0.5 * dps
+    assert (np.abs(p[sel] - pan) / dps).max() < 0.06

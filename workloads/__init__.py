@@ -43,6 +43,8 @@ __all__ = [
     "faulted_aquifer",
     "TetProblem",
     "cryer_octant",
+    "FaultedTetProblem",
+    "tetrahedralize",
     "column_terzaghi",
     "theis_plate",
     "tiny_faulted",
@@ -517,6 +519,98 @@ def tiny_faulted(nx: int = 2, ny: int = 2, nz: int = 2, shear=(0.0, 0.0), k_perp
                    h=tuple(h), shear=tuple(shear), kf=kf, fault=fault, E=E, k=k, nu=0.25,
                    alpha=0.8, M=50e9, mu_f=1e-3, fixed=fixed, fu=fu, fp=fp,
                    dts=[dt] * steps, notes="small faulted box")
+
+
+@dataclasses.dataclass
+class FaultedTetProblem:
+    """A P1-tetrahedron problem with one planar fault of duplicated nodes.
+
+    pairs[i] = (minus node, plus node) of fault node pair i; fault_tris holds
+    the triangles of the fault surface as triples of pair ids, ordered so
+    that the right-hand-rule normal points from the minus to the plus lip.
+    t1_ref is the direction whose projection onto the fault is the first
+    tangent t1 (tau0 is given in the frame t1, t2 = n x t1).  E and k are
+    per tetrahedron; fixed, fu, fp and dts as in Problem."""
+
+    name: str
+    nodes: np.ndarray       # (N, 3) coordinates [m]; both lips at the same place
+    tets: np.ndarray        # (M, 4) vertex ids, positive orientation
+    pairs: np.ndarray       # (P, 2) node ids (minus, plus)
+    fault_tris: np.ndarray  # (T, 3) pair ids, minus-to-plus right-hand order
+    t1_ref: tuple
+    fault: FaultParams
+    E: np.ndarray           # (M,) [Pa]
+    k: np.ndarray           # (M,) [m^2]
+    nu: float
+    alpha: float
+    M: float
+    mu_f: float
+    fixed: np.ndarray       # uint8 (4, N)
+    fu: np.ndarray          # (3, N)
+    fp: np.ndarray          # (N,)
+    dts: list
+    notes: str = ""
+
+    @property
+    def n_nodes(self) -> int:
+        return self.nodes.shape[0]
+
+
+_KUHN_PATHS = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+
+
+def tetrahedralize(prob: Problem, t1_ref=(1.0, 0.0, 0.0)) -> FaultedTetProblem:
+    """The same faulted box on linear tetrahedra (the paper's element, Sec. 3.1):
+    every hexahedron of the structured grid is cut into the six Kuhn
+    tetrahedra along its diagonal from local corner (0,0,0) to (1,1,1), which
+    is conforming between cells and cuts every fault quad along the same
+    diagonal, into the triangles (b0, b1, b3) and (b0, b3, b2) of its corner
+    pairs b = bx + 2 by.  Node numbering, lips, constraints, loads, sources,
+    steps and fault parameters are those of ``prob``; each tetrahedron takes
+    the E and k of its hexahedron."""
+    nx, ny, nz, kf = prob.nx, prob.ny, prob.nz, prob.kf
+    if kf is None:
+        raise ValueError("tetrahedralize expects a faulted problem")
+    nb = (nx + 1) * (ny + 1)
+    npl = n_planes(nz, kf)
+    kk, j, i = np.meshgrid(np.arange(npl), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    i, j, kk = i.ravel(), j.ravel(), kk.ravel()
+    korig = np.where(kk > kf, kk - 1, kk)
+    hx, hy, hz = prob.h
+    sx, sy = prob.shear
+    ox, oy, oz = prob.origin
+    nodes = np.stack([ox + i * hx, oy + j * hy,
+                      oz + korig * hz + sx * i * hx + sy * j * hy], axis=1)
+    ei, ej, ek = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    ei, ej, ek = (a.transpose(2, 1, 0).ravel() for a in (ei, ej, ek))   # element id order
+    kb = ek + (ek >= kf)
+    tets = []
+    for path in _KUHN_PATHS:
+        v = [0, 0, 0]
+        corners = [node_id(nx, ny, ei, ej, kb)]
+        for ax in path:
+            v[ax] += 1
+            corners.append(node_id(nx, ny, ei + v[0], ej + v[1], kb + v[2]))
+        tets.append(np.stack(corners, axis=1))
+    tets = np.stack(tets, axis=1).reshape(-1, 4)                          # 6 per hex, hex-major
+    a, b, c, d = (nodes[tets[:, q]] for q in range(4))
+    neg = np.einsum("ij,ij->i", np.cross(b - a, c - a), d - a) < 0
+    tets[neg, 1], tets[neg, 2] = tets[neg, 2].copy(), tets[neg, 1].copy()
+    pid = np.arange(nb)
+    pairs = np.stack([pid + nb * kf, pid + nb * (kf + 1)], axis=1)
+    qi, qj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    qi, qj = qi.ravel(), qj.ravel()
+    b0 = qi + (nx + 1) * qj
+    b1, b2, b3 = b0 + 1, b0 + (nx + 1), b0 + (nx + 2)
+    tris = np.concatenate([np.stack([b0, b1, b3], 1), np.stack([b0, b3, b2], 1)])
+    E = np.repeat(np.broadcast_to(np.asarray(prob.E, float), (prob.n_el,)), 6)
+    k = np.repeat(np.broadcast_to(np.asarray(prob.k, float), (prob.n_el,)), 6)
+    return FaultedTetProblem(name=prob.name + "_tet", nodes=nodes, tets=tets, pairs=pairs,
+                             fault_tris=tris, t1_ref=tuple(float(x) for x in t1_ref),
+                             fault=prob.fault, E=E, k=k, nu=prob.nu, alpha=prob.alpha, M=prob.M,
+                             mu_f=prob.mu_f, fixed=prob.fixed.copy(), fu=prob.fu.copy(),
+                             fp=prob.fp.copy(), dts=list(prob.dts),
+                             notes=prob.notes + "; Kuhn tetrahedra")
 
 
 def random_vectors(n_nodes: int, seed: int, scale_u: float = 1e-4, scale_p: float = 1e6):
