@@ -73,6 +73,63 @@ int gm_tet_surface_load(gm_tet* t, const int64_t* tris_host, int64_t n_tris, dou
 int gm_tet_step(gm_tet* t, double dt, double* u_dev, double* p_dev, double rtol, int maxit,
                 gm_solve_report* report_host, void* stream);
 
+/* ---- Fault on the tetrahedral mesh (Sec. 3.1.1-3.1.2: interface elements on
+ * the triangles of the fault surface) ------------------------------------- */
+
+/* One planar fault of duplicated nodes.  pairs_host holds 2*n_pairs node ids,
+ * the minus lips first (pairs_host[i]) then the plus lips (pairs_host[P + i]);
+ * a node belongs to at most one pair, and no tetrahedron holds both lips of a
+ * pair.  tris_host holds 3*n_tris pair ids, one triangle of the fault surface
+ * each, ordered so that the right-hand-rule normal points from the minus to
+ * the plus lip.  t1_ref_host (3 values) is the direction whose projection on
+ * the fault gives the first tangent t1 (tau0 is given in t1, t2 = n x t1).
+ * Computed here from the minus-lip coordinates: the tributary area A_i = sum
+ * of area/3 over the pair's triangles (nodal quadrature), the normal = the
+ * normalised area-weighted sum of its triangles' normals, and each triangle's
+ * longitudinal Laplacian.  k_perp <= 0 ties the two lip pressures (the plus
+ * lip's pressure then equals the minus lip's and carries no equation).
+ * Resets the fault history (inelastic slip 0).  GM_EINVAL for ids out of
+ * range, a node in two pairs, a degenerate triangle, a pair on no triangle or
+ * t1_ref normal to the fault.  Synchronises. */
+int gm_tet_fault(gm_tet* t, const int64_t* pairs_host, int64_t n_pairs, const int64_t* tris_host,
+                 int64_t n_tris, const double* t1_ref_host, const gm_fault_params* params_host);
+
+/* Nodal loads for gm_tet_fault_step: f^u (3*N forces [N]) and f^p (N fluid
+ * sources [m^3/s]); either may be NULL (zero).  Replaces the forces of
+ * gm_tet_surface_load.  A source on a tied plus-lip node is added to its
+ * minus-lip partner. */
+int gm_tet_loads(gm_tet* t, const double* fu_host, const double* fp_host);
+
+/* y = A x with the fault terms, FP64, for which = GM_OP_KT (bulk K plus the
+ * cohesive tangent of the last return map; zero before the first step),
+ * GM_OP_APU, GM_OP_AUP or GM_OP_A22 (S + dt C with fault storage, the
+ * triangles' longitudinal flow and, untied, the transverse term).  Pressure
+ * vectors live in the tied space: the plus-lip entry of a tied pair is an
+ * unknown of no equation, ignored on input and 0 on output.  Constrained
+ * entries of x are ignored and those of y are 0. */
+int gm_tet_fault_apply(gm_tet* t, int which, const double* x_dev, double* y_dev, double dt, void* stream);
+
+/* One implicit step with the fault (Sec. 3.3.1): Newton on the incremental
+ * residuals with the contact / Coulomb return map at every pair (Sec. 2.2.1),
+ * each correction by Prevost's partitioned CG (Sec. 3.3.2) with inner K_T
+ * solves by PCG with nodal 3x3 block Jacobi (the blocks include the pair's
+ * cohesive tangent) and the diagonal of S + dt C as the outer preconditioner.
+ * Stops when the fault states of two successive iterations agree and
+ * rhat <= newton_rtol * max(rhat0, 1e-3 shat), with rhat the residual scaled
+ * by the diagonals of K and S + dt C.  u_dev (3N) and p_dev (N) hold the
+ * accepted state on entry and the new one on return (tied plus lips carry
+ * their partner's pressure).  Uses newton_rtol, newton_maxit, outer_rtol,
+ * outer_maxit, inner_rtol and inner_maxit of opts (FP64 only).  GM_ENEWTON
+ * at the Newton limit, GM_ENOCONV at a CG limit; the state is then unchanged.
+ * Synchronises. */
+int gm_tet_fault_step(gm_tet* t, double dt, double* u_dev, double* p_dev, const gm_step_opts* opts_host,
+                      gm_step_report* report_host, void* stream);
+
+/* Fault state after the last accepted step, any pointer may be NULL:
+ * flags (P: GM_OPEN / GM_STICK / GM_SLIP), slip (2P, field-major: the jump
+ * [[u]] projected on t1, then on t2), inelastic slip (2P, same layout). */
+int gm_tet_fault_state(gm_tet* t, int8_t* flags_host, double* slip_host, double* dlie_host);
+
 #ifdef __cplusplus
 }
 #endif

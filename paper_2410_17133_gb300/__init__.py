@@ -101,6 +101,11 @@ _SIG = {
     "gm_tet_dirichlet": (C.c_int, [_P, C.POINTER(C.c_uint8), C.c_int64]),
     "gm_tet_surface_load": (C.c_int, [_P, _P, C.c_int64, C.c_double]),
     "gm_tet_step": (C.c_int, [_P, C.c_double, _P, _P, C.c_double, C.c_int, C.POINTER(SolveReport), _P]),
+    "gm_tet_fault": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _D, C.POINTER(FaultParams)]),
+    "gm_tet_loads": (C.c_int, [_P, _D, _D]),
+    "gm_tet_fault_apply": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, _P]),
+    "gm_tet_fault_step": (C.c_int, [_P, C.c_double, _P, _P, C.POINTER(StepOpts), C.POINTER(StepReport), _P]),
+    "gm_tet_fault_state": (C.c_int, [_P, C.POINTER(C.c_int8), _D, _D]),
     "gm_set_preconditioner": (C.c_int, [_P, C.c_int]),
     "gm_adjoint_sweep_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _D,
                                         C.c_double, C.c_int, C.POINTER(SolveReport), _P]),
@@ -536,6 +541,76 @@ class TetSolver:
         assert x.is_contiguous() and y.is_contiguous() and y.dtype == x.dtype
         self._chk(self._L.gm_tet_apply(self.h, w, _tptr(x), _tptr(y), float(dt), dt_code, _stream_ptr(stream)))
         return y
+
+
+class TetFaultSolver(TetSolver):
+    """P1 tetrahedra with one fault of duplicated nodes and interface elements
+    on its triangles (include/gm_tet.h, gm_tet_fault*): argument marshalling
+    only.  The state (u (3, N), p (N,)) lives in CUDA float64 tensors owned
+    here; the fault history lives in the library."""
+
+    def fault(self, pairs, tris, t1_ref, params):
+        pr = np.ascontiguousarray(np.asarray(pairs, np.int64).T).reshape(-1)
+        tr = np.ascontiguousarray(tris, np.int64).reshape(-1)
+        r = np.ascontiguousarray(t1_ref, np.float64)
+        if isinstance(params, FaultParams):
+            fp = params
+        else:
+            if np.ndim(params.tn0) > 0 or np.ndim(params.tau0) > 1:
+                raise ValueError("the tetrahedral fault takes uniform in-situ tractions")
+            fp = FaultParams(params.kn, params.ks, params.f, params.w0, params.wk_par, params.k_perp,
+                             params.MF, float(params.tn0), (C.c_double * 2)(*params.tau0))
+        self._chk(self._L.gm_tet_fault(self.h, pr.ctypes.data_as(C.c_void_p), pr.size // 2,
+                                       tr.ctypes.data_as(C.c_void_p), tr.size // 3, _dptr(r), C.byref(fp)))
+        self.P = pr.size // 2
+
+    def loads(self, fu=None, fp=None):
+        a = None if fu is None else np.ascontiguousarray(fu, np.float64).reshape(-1)
+        b = None if fp is None else np.ascontiguousarray(fp, np.float64).reshape(-1)
+        self._chk(self._L.gm_tet_loads(self.h, None if a is None else _dptr(a), None if b is None else _dptr(b)))
+
+    def fault_apply(self, which, x, dt=0.0, stream=None):
+        """gm_tet_fault_apply for which in ('KT', 'APU', 'AUP', 'A22'); float64 CUDA tensors."""
+        import torch
+        w = OP[which] if isinstance(which, str) else int(which)
+        y = torch.empty({1: (3, self.N), 2: (self.N,), 3: (3, self.N), 4: (self.N,)}[w], dtype=torch.float64,
+                        device=x.device)
+        assert x.dtype == torch.float64 and x.is_contiguous()
+        self._chk(self._L.gm_tet_fault_apply(self.h, w, _tptr(x), _tptr(y), float(dt), _stream_ptr(stream)))
+        return y
+
+    def fault_step(self, dt, u, p, newton_rtol=1e-12, newton_maxit=50, outer_rtol=1e-11, outer_maxit=5000,
+                   inner_rtol=1e-13, inner_maxit=20000, stream=None):
+        """gm_tet_fault_step: u (3, N), p (N,) float64 CUDA tensors updated in place."""
+        o = StepOpts(newton_rtol, newton_maxit, outer_rtol, outer_maxit, inner_rtol, inner_maxit, F64, 0)
+        rep = StepReport()
+        self._chk(self._L.gm_tet_fault_step(self.h, float(dt), _tptr(u), _tptr(p), C.byref(o), C.byref(rep),
+                                            _stream_ptr(stream)))
+        return rep.as_dict()
+
+    def fault_state(self):
+        flags = np.zeros(self.P, np.int8)
+        slip = np.zeros(2 * self.P)
+        dlie = np.zeros(2 * self.P)
+        self._chk(self._L.gm_tet_fault_state(self.h, flags.ctypes.data_as(C.POINTER(C.c_int8)), _dptr(slip),
+                                             _dptr(dlie)))
+        return dict(flags=flags, slip=slip.reshape(2, self.P).T.copy(), dlie=dlie.reshape(2, self.P).T.copy())
+
+    @classmethod
+    def from_problem(cls, prob, device: int = 0):
+        """A workloads.FaultedTetProblem: mesh, uniform materials, constraints,
+        loads and the fault."""
+        E = np.asarray(prob.E, float)
+        k = np.asarray(prob.k, float)
+        if np.any(E != E.flat[0]) or np.any(k != k.flat[0]):
+            raise ValueError("the tetrahedral path takes uniform E and k")
+        s = cls(device)
+        s.mesh(prob.nodes, prob.tets)
+        s.materials(E.flat[0], prob.nu, prob.alpha, prob.M, k.flat[0], prob.mu_f)
+        s.dirichlet(prob.fixed)
+        s.loads(prob.fu, prob.fp)
+        s.fault(prob.pairs, prob.fault_tris, prob.t1_ref, prob.fault)
+        return s
 
 
 def run_with_adjoint(solver, dts, objective_grad, checkpoint_every=5, step_kw=None, rtol=1e-10, maxit=300):
