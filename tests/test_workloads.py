@@ -32,3 +32,29 @@ def test_faulted_aquifer_frame_source_and_layers():
     assert np.unique(p.E).tolist() == [15e9, 25e9, 40e9]
     k_aq = p.k[p.E == 15e9]
     assert k_aq.min() > 1e-16 and p.k[p.E == 25e9].max() == 1e-19
+
+
+def test_marginally_pressurised_case_matches_the_printed_parameters():
+    """The T = 4 workload restates the paper's marginally pressurised case
+    (Sec. 4.2, Table 1; golden file): tau0, sigma'_0, Q and the Table-1 fault
+    values as printed, T = 4 from them within the printing's 2e-3, and a time
+    schedule whose pressure front ends near 10 m (inside the 20 m half-width)
+    with the closed-form rupture radius lambda(4) L spanning at least 8 cells."""
+    import json
+    import math
+    import os
+    from oracle import analytic as A
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "table1_slip_benchmark.json")))
+    p = W.marginally_pressurised()
+    fp = p.fault
+    assert abs(fp.tau0[0] / g["tau0_MP"] - 1) < 1e-12        # tau0 = ratio * f * sigma'_0
+    assert fp.tn0 == g["sigma0"] and fp.f == g["f"]
+    assert (fp.kn, fp.ks, fp.wk_par, fp.MF) == (g["kn"], g["ks"], g["wk_par"], g["MF"])
+    assert abs(p.fp.sum() / g["Q"] - 1) < 1e-12
+    assert p.mu_f == g["mu_f"] and p.E[0] == g["E"] and p.nu == g["nu"] and p.alpha == g["alpha"]
+    T = A.stress_injection_parameter(fp.tau0[0], fp.f, fp.tn0, p.fp.sum(), p.mu_f, fp.wk_par)
+    assert abs(T / g["T_MP"] - 1) < 2e-3
+    D = A.fault_diffusivity(fp.wk_par, fp.MF, p.mu_f, fp.w0)
+    L = math.sqrt(4 * D * sum(p.dts))
+    assert 9.5 < L < 10.5 < g["box"] / 2
+    assert A.lambda_of_T(T) * L / p.h[0] > 8.0

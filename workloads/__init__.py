@@ -37,6 +37,7 @@ __all__ = [
     "n_planes",
     "fault_small",
     "slip_front",
+    "marginally_pressurised",
     "inclined_lognormal",
     "adjoint_lognormal",
     "adjoint_objective",
@@ -214,6 +215,27 @@ def slip_front(n: int = 64, steps: int = 50, ratio: float = 0.99, T: float = 0.1
                    kf=kf, fault=fault, E=np.full(nel, 60e9), k=np.zeros(nel),
                    nu=0.0, alpha=0.0, M=1e14, mu_f=mu, fixed=fixed, fu=fu, fp=fp,
                    dts=dts, notes=f"ratio={ratio} T={T} Q={Q:.6e}")
+
+
+def marginally_pressurised(n: int = 256, steps: int = 64, dt0: float = 1.0,
+                           growth: float = 1.119) -> Problem:
+    """The marginally pressurised case of Sec. 4.2 (Table 1 values): tau0 =
+    47.830 MPa against f sigma'_0 = 48 MPa and Q = 1e-6 m^3/s, i.e. the
+    stress-injection parameter T = 4, on the 40 m cube of ``slip_front`` with
+    n^3 hexes.  The rupture front stays far behind the pressure front here
+    (R = lambda(4) L with lambda(4) = 0.139), so the grid must be fine: with
+    n = 256 and the geometric steps dt_k = dt0 growth^k the pressure front
+    reaches L = 10 m (half the half-width) near the last step, where R spans
+    about nine cells."""
+    sig0, tau0 = 80e6, 47.830e6
+    mu, wk = 0.89e-3, 1e-15
+    Q = 1e-6
+    dpstar = Q * mu / (4.0 * math.pi * wk)
+    T = (1.0 - tau0 / (0.6 * sig0)) * sig0 / dpstar
+    prob = slip_front(n=n, steps=steps, ratio=tau0 / (0.6 * sig0), T=T, dt0=dt0, growth=growth)
+    prob.name = f"marginal{n}"
+    prob.notes = f"tau0={tau0} Q={Q} T={T:.4f}"
+    return prob
 
 
 def inclined_lognormal(n: int = 160, steps: int = 20, seed: int = 3,
