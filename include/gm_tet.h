@@ -100,8 +100,10 @@ int gm_tet_fault(gm_tet* t, const int64_t* pairs_host, int64_t n_pairs, const in
  * minus-lip partner. */
 int gm_tet_loads(gm_tet* t, const double* fu_host, const double* fp_host);
 
-/* y = A x with the fault terms, FP64, for which = GM_OP_KT (bulk K plus the
- * cohesive tangent of the last return map; zero before the first step),
+/* y = A x with the fault terms (Sec. 3.2.3 and App. B: A^f_pu, its transpose
+ * A^f_up, fracture storage, longitudinal and transverse flow), FP64, for
+ * which = GM_OP_KT (bulk K plus the cohesive tangent of the last return map,
+ * Sec. 3.3.1; zero before the first step),
  * GM_OP_APU, GM_OP_AUP or GM_OP_A22 (S + dt C with fault storage, the
  * triangles' longitudinal flow and, untied, the transverse term).  Pressure
  * vectors live in the tied space: the plus-lip entry of a tied pair is an

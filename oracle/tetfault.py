@@ -38,7 +38,9 @@ from .tet import tet_element_matrices
 
 def triangle_fault_geometry(nodes, pairs, tris, t1_ref):
     """Per pair: tributary area, unit normal (minus -> plus), tangents; per
-    triangle: area and the unit-coefficient Laplacian a_t G_t G_t^T (T, 3, 3)."""
+    triangle: area and the unit-coefficient Laplacian a_t G_t G_t^T (T, 3, 3).
+    Sec. 3.1.1 (interface element geometry, averaged facet normals) and Sec.
+    3.2.3 (longitudinal fracture flow), on linear triangles."""
     X = nodes[pairs[tris, 0]]                                   # (T, 3, 3) minus lip
     e1 = X[:, 1] - X[:, 0]
     e2 = X[:, 2] - X[:, 0]
@@ -71,7 +73,9 @@ def _coo(rows, cols, vals, shape):
 class TetFaultModel:
     """Assembled operators of a FaultedTetProblem, with the attributes the
     Newton loop of solve.py reads (N, prob, fg, Kb, Apu, S, C, free_u, free_p,
-    fu, fpv, dK, A22, jump, expand_p)."""
+    fu, fpv, dK, A22, jump, expand_p): the bulk P1 operators of Sec. 3.2 and
+    App. A, and the fault blocks of Sec. 3.2.3 and App. B (A^f_pu read as the
+    transpose of A^f_up, storage w/M_F, tied or transverse lip pressures)."""
 
     def __init__(self, prob):
         self.prob = prob
