@@ -1,8 +1,9 @@
 /*
  * gm_tet.h - operators of the paper's own discretisation on unstructured
  * meshes: linear (P1) tetrahedra for displacement and pressure (Sec. 3.1:
- * linear shape functions on tetrahedra for both fields), without fault
- * elements.  Used for Cryer's sphere (Sec. 4.1).
+ * linear shape functions on tetrahedra for both fields), used for Cryer's
+ * sphere (Sec. 4.1), and a fault of duplicated nodes with interface elements
+ * on its triangles (Sec. 3.1.1-3.1.2) stepped by Newton (Sec. 3.3.1).
  *
  * Conventions are those of gm.h (status codes, *_host / *_dev pointers,
  * stream as void*, field-major vectors: u as [ux | uy | uz] of 3*N values,

@@ -24,8 +24,8 @@ Pinned by: tests/test_oracle_tetfault.py (fault area, normal and frame of a
 sheared plane; Laplacian kernel and linear-field energy; rigid modes 12 / 6
 for an open / stuck fault; nodal forces of a constant stress at the lips
 against -/+ A_i sigma n; uniform lip pressure force and aperture volume;
-line-source fault pressure within 5 %; dense LU = Prevost CG on the Newton
-step).
+line-source pressure front within the paper's 8 % and profile within 6 % of
+dp*; dense LU = Prevost CG on the Newton step).
 """
 from __future__ import annotations
 
