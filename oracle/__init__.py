@@ -27,9 +27,12 @@ Fluid-induced Fault Slip in Poroelastic Media") defines:
   tetfault.py  P1 tetrahedra with a fault: interface elements on the fault
                triangles (Sec. 3.1.1-3.1.2), nodal quadrature per pair, the
                triangle Laplacian; stepped by solve.py's Newton unchanged.
-  rows.py      the same operators evaluated one node at a time, for sampled
-               checks on meshes too large to assemble.
+  adjoint.py   gradients of an objective of the converged steps (frozen
+               fault states, consistent return-map derivative), one step and
+               several steps with the inelastic slip as history.
 
-Parity status per function is stated in each docstring ("pinned by ..." or
-"parity unpinned").
+Each module's header names the tests that pin it ("Pinned by: ...").  Parity
+unpinned: the transient slip field at finite k_s on a finite box with Biot
+coupling has no closed form; it is pinned only through the limits above and
+the agreement of the independent solvers.
 """

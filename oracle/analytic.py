@@ -38,6 +38,11 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
      xi h'(xi) = (xi cot xi + xi^2 / sin^2 xi - 2) / xi^2,
   over the positive roots of (1 - eta xi^2) tan xi = xi, eta = (1 + beta)/(3 beta).
   The reduced equation is also solved by radial finite volumes (the pin).
+
+Pinned by: tests/test_oracle_analytic.py (lambda(T) limits for small and large
+T, the consolidation series at t = 0 and late times, the scale dp*) and
+tests/test_golden.py (T of the printed cases); Cryer's series against the
+radial finite volumes in tests/test_oracle_tet.py.
 """
 from __future__ import annotations
 

@@ -11,6 +11,13 @@ hexahedra (Q1) and bilinear fault quadrilaterals on a structured, possibly
 affinely sheared grid (Sec. 3.1 states other standard elements may be used).
 
 Global DOF layout inside the oracle: u component-major, dof = c * N + n; p dof = n.
+
+Pinned by: tests/test_oracle_element.py (symmetry and the 6 rigid-body modes of
+the element stiffness on box and sheared cells; exact strain, Biot, storage and
+Darcy energies of linear fields; global patch tests for elasticity and flow;
+null space 6 / 12 with the fault stuck / open; fault area, normals and frame;
+uniform lip pressure force and aperture volume) and, through the solvers, the
+consolidation and line-source tests of tests/test_oracle_solvers.py.
 """
 from __future__ import annotations
 

@@ -22,6 +22,12 @@ is the same scaling applied to the current total state and to F0, the nodal
 force of the in-situ fault tractions (+/- A_i (-t'_n0 n + tau0) on the lips);
 all terms have units of energy.  The shat term only sets a floor near the
 rounding level of the residual evaluation when a step changes little.
+
+Pinned by: tests/test_oracle_solvers.py (dense LU = sparse direct = Prevost CG
+on faulted boxes, tied and untied; Newton paths equal across the linear
+solvers; the unit-cube case reaches open, stick and slip without near-ties;
+1-D consolidation against the series at second order; line-source pressure
+front within the paper's 8 %).
 """
 from __future__ import annotations
 

@@ -14,6 +14,11 @@ Global vectors are field-major like the structured oracle: u = [ux | uy | uz],
 p.  The time step is the backward-Euler monolithic system of Sec. 3.3 without
 fault terms, solved directly (sparse LU plus two steps of iterative refinement):
   K u - A p = f,   A^T (u - u_n) + S (p - p_n) + dt C p = 0.
+
+Pinned by: tests/test_oracle_tet.py (symmetry and rigid modes; exact strain
+energy, Biot work, storage energy against an independent quadrature and Darcy
+energy of linear fields; assembled patch identities and the surface-load
+resultant on the Cryer octant; Cryer's centre pressure within the paper's 4 %).
 """
 from __future__ import annotations
 
