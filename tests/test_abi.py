@@ -36,3 +36,11 @@ def test_binding_refuses_missing_library(tmp_path):
             gm.load_library(str(tmp_path / "nope.so"))
     finally:
         gm._lib = saved
+
+
+def test_binding_types_every_declared_call():
+    """Every entry point the headers declare has a typed ctypes signature in
+    the binding (argument marshalling only), and the binding declares nothing
+    the headers do not."""
+    import paper_2410_17133_gb300 as gm
+    assert set(declared_symbols()) == set(gm._SIG)
