@@ -58,3 +58,43 @@ def test_marginally_pressurised_case_matches_the_printed_parameters():
     L = math.sqrt(4 * D * sum(p.dts))
     assert 9.5 < L < 10.5 < g["box"] / 2
     assert A.lambda_of_T(T) * L / p.h[0] > 8.0
+
+
+def test_stress_rotation_matches_the_papers_orientation_statements():
+    """Sec. 5's stress-rotation study: rotating the horizontal stresses by beta
+    from the strike, the Coulomb ratio |tau0| / (f t'_n0) of the fault is
+    smallest at beta = 90 (the larger horizontal stress across the fault, the
+    paper's most stable orientation) and largest between 20 and 40 degrees
+    and, mirrored, between 140 and 160 (the paper: slip is promoted around 30
+    and 150); beta and 180 - beta give the same ratio; beta = 0 is the default
+    set-up; and the rotated tractions equal the rotated tensor projected on
+    the oracle's fault frame."""
+    def ratio(beta):
+        p = W.faulted_aquifer(nv=20, ny=2, nz=2, steps=1, Q=0.5, beta_deg=beta)
+        return float(np.max(np.linalg.norm(p.fault.tau0, axis=1) / (p.fault.f * p.fault.tn0)))
+    bs = np.arange(0.0, 180.5, 1.0)
+    rs = np.array([ratio(b) for b in bs])
+    assert bs[np.argmin(rs)] == 90.0
+    first = bs[np.argmax(np.where(bs < 90, rs, -1))]
+    second = bs[np.argmax(np.where(bs > 90, rs, -1))]
+    assert 20.0 <= first <= 40.0 and 140.0 <= second <= 160.0
+    assert np.allclose(rs, rs[::-1], rtol=1e-12)
+    d0 = W.faulted_aquifer(nv=20, ny=6, nz=8, steps=1, Q=0.5)
+    d1 = W.faulted_aquifer(nv=20, ny=6, nz=8, steps=1, Q=0.5, beta_deg=0.0)
+    assert np.array_equal(d0.fault.tn0, d1.fault.tn0) and np.array_equal(d0.fault.tau0, d1.fault.tau0)
+    p = W.faulted_aquifer(nv=20, ny=6, nz=8, steps=1, Q=0.5, beta_deg=30.0)
+    mesh = fem.Mesh(p.nx, p.ny, p.nz, p.origin, p.h, p.shear, p.kf)
+    fg = fem.fault_geometry(mesh)
+    depth = 500.0 + 2000.0 - (np.arange(p.n_pairs) % (p.nx + 1)) * p.h[0]
+    p0 = 9.81e3 * depth
+    b = np.radians(30.0)
+    Rz = np.array([[1.0, 0.0, 0.0], [0.0, np.cos(b), -np.sin(b)], [0.0, np.sin(b), np.cos(b)]])
+    S = np.zeros((p.n_pairs, 3, 3))
+    S[:, 0, 0] = -(18.75e3 * depth - p0)
+    S[:, 1, 1] = -(20.4e3 * depth - p0)
+    S[:, 2, 2] = -(11.9e3 * depth - p0)
+    S = np.einsum("ij,pjk,lk->pil", Rz, S, Rz)
+    tr = np.einsum("pij,pj->pi", S, fg["n"])
+    assert np.allclose(-np.sum(tr * fg["n"], 1), p.fault.tn0, rtol=1e-12)
+    assert np.allclose(np.sum(tr * fg["t1"], 1), p.fault.tau0[:, 0], rtol=1e-10, atol=1e-6)
+    assert np.allclose(np.sum(tr * fg["t2"], 1), p.fault.tau0[:, 1], rtol=1e-10, atol=1e-6)

@@ -296,7 +296,7 @@ def adjoint_objective(prob: Problem, n_slip: int = 256, n_p: int = 64, seed: int
 
 def faulted_aquifer(nv: int = 128, ny: int = 256, nz: int = 256, steps: int = 100, seed: int = 5,
                     dt: float = 43200.0, Q: float = 0.01, throw: float = 150.0,
-                    dip_deg: float = 80.0, sv_grad: float = 18.75e3) -> Problem:
+                    dip_deg: float = 80.0, sv_grad: float = 18.75e3, beta_deg: float = 0.0) -> Problem:
     """Faulted aquifer (Sec. 5 restated): 2000 m (vertical) x 4000 m x 4000 m.
 
     Grid axes: x is vertical (x = 0 at the bottom, H = 2000 m at the top, nv
@@ -317,7 +317,11 @@ def faulted_aquifer(nv: int = 128, ny: int = 256, nz: int = 256, steps: int = 10
     pair, t'_n0 = -n.S'n and tau0 = (t1.S'n, t2.S'n) with S' the tension-positive
     effective stress and (n, t1, t2) the library's fault frame (n from the
     grid-z < kf side to the other, t1 the unit grid-x direction in the plane,
-    t2 = n x t1).  Injection Q as a line source over the hanging-wall aquifer at
+    t2 = n x t1).  beta_deg rotates the two horizontal principal stresses about
+    the vertical by beta, the 20.4 kPa/m one from the strike towards the fault
+    normal (Sec. 5's stress-rotation study; beta = 0 is the default set-up, 90
+    puts the larger horizontal stress across the fault).  Injection Q as a line
+    source over the hanging-wall aquifer at
     mid-strike, 250 m from the fault, split by nodal length.  Bottom face
     u = 0, all faces no-flow."""
     H, Ly, Lz = 2000.0, 4000.0, 4000.0
@@ -352,8 +356,12 @@ def faulted_aquifer(nv: int = 128, ny: int = 256, nz: int = 256, steps: int = 10
     p0 = 9.81e3 * depth
     S = np.zeros((P, 3, 3))            # tension-positive effective stress, physical axes
     S[:, 0, 0] = -(sv_grad * depth - p0)
-    S[:, 1, 1] = -(20.4e3 * depth - p0)
-    S[:, 2, 2] = -(11.9e3 * depth - p0)
+    sH = -(20.4e3 * depth - p0)
+    sh = -(11.9e3 * depth - p0)
+    cb, sb = math.cos(math.radians(beta_deg)), math.sin(math.radians(beta_deg))
+    S[:, 1, 1] = cb * cb * sH + sb * sb * sh
+    S[:, 2, 2] = sb * sb * sH + cb * cb * sh
+    S[:, 1, 2] = S[:, 2, 1] = cb * sb * (sH - sh)
     tr = S @ n_
     tn0 = -(tr @ n_)
     tau0 = np.stack([tr @ t1, tr @ t2], 1)
@@ -370,7 +378,7 @@ def faulted_aquifer(nv: int = 128, ny: int = 256, nz: int = 256, steps: int = 10
     return Problem(name=f"aquifer{nv}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, origin=(0.0, 0.0, -Lz / 2),
                    h=(hx, hy, hz), shear=(sx, 0.0), kf=kf, fault=fault, E=E, k=k, nu=0.15,
                    alpha=0.64, M=22.7e9, mu_f=0.89e-3, fixed=fixed, fu=fu, fp=fp,
-                   dts=[dt] * steps, notes=f"seed={seed} dip={dip_deg} throw={throw}")
+                   dts=[dt] * steps, notes=f"seed={seed} dip={dip_deg} throw={throw} beta={beta_deg}")
 
 
 @dataclasses.dataclass
