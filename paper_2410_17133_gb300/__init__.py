@@ -613,6 +613,24 @@ class TetFaultSolver(TetSolver):
         return s
 
 
+def run_until_slip(solver, dts, Q, step_kw=None):
+    """Step through dts until the first pair is in the slipping state (the
+    onset of inelastic slip, Sec. 5) and return (steps taken, elapsed time,
+    injected volume Q * time, final state); (len(dts), t, Q t, state) with
+    state["flags"] free of slip if no pair slipped.  Sequences library calls
+    only: solver.step(dt, **step_kw) and solver.get_state()."""
+    kw = dict(step_kw or {})
+    t = 0.0
+    st = None
+    for n, dt in enumerate(dts):
+        solver.step(dt, **kw)
+        t += dt
+        st = solver.get_state()
+        if np.any(np.asarray(st["flags"]) == SLIP):
+            return n + 1, t, Q * t, st
+    return len(dts), t, Q * t, st
+
+
 def run_with_adjoint(solver, dts, objective_grad, checkpoint_every=5, step_kw=None, rtol=1e-10, maxit=300):
     """Run len(dts) implicit steps from the solver's current state, then the
     reverse sweep of the multi-step adjoint (inelastic slip as history).
