@@ -35,7 +35,7 @@ const char* gm_tet_last_error(const gm_tet* t);
  * volumes are computed here (FP64, FP32 copy); the node-to-element incidence
  * is stored so that each node gathers its elements in a fixed order
  * (deterministic results).  GM_EINVAL for ids out of range, a degenerate
- * tetrahedron, or sizes beyond 2^29 nodes or tetrahedra.  Synchronises. */
+ * tetrahedron, or sizes beyond 2^27 nodes or tetrahedra.  Synchronises. */
 int gm_tet_mesh(gm_tet* t, const double* nodes_host, int64_t n_nodes, const int64_t* tets_host,
                 int64_t n_tets);
 
@@ -90,8 +90,8 @@ int gm_tet_step(gm_tet* t, double dt, double* u_dev, double* p_dev, double rtol,
  * longitudinal Laplacian.  k_perp <= 0 ties the two lip pressures (the plus
  * lip's pressure then equals the minus lip's and carries no equation).
  * Resets the fault history (inelastic slip 0).  GM_EINVAL for ids out of
- * range, a node in two pairs, a degenerate triangle, a pair on no triangle or
- * t1_ref normal to the fault.  Synchronises. */
+ * range, a node in two pairs, a degenerate triangle, a pair on no triangle,
+ * t1_ref normal to the fault, or more than 2^27 triangles.  Synchronises. */
 int gm_tet_fault(gm_tet* t, const int64_t* pairs_host, int64_t n_pairs, const int64_t* tris_host,
                  int64_t n_tris, const double* t1_ref_host, const gm_fault_params* params_host);
 

@@ -190,7 +190,8 @@ int gm_tet_mesh(gm_tet* t, const double* nodes, int64_t n_nodes, const int64_t* 
 {
     if (!t) return GM_EINVAL;
     if (!nodes || !tets || n_nodes < 4 || n_tets < 1) return t->set_err(GM_EINVAL, "tet mesh: empty mesh");
-    if (n_nodes > (1LL << 29) || n_tets > (1LL << 29)) return t->set_err(GM_EINVAL, "tet mesh: too large");
+    // the kernels index element and nodal-block arrays (12 M, 9 N entries) with 32-bit ints
+    if (n_nodes > (1LL << 27) || n_tets > (1LL << 27)) return t->set_err(GM_EINVAL, "tet mesh: too large");
     const long long N = n_nodes, M = n_tets;
     std::vector<double> G(12 * M), V(M);
     std::vector<int> tv(4 * M);
@@ -1204,7 +1205,7 @@ extern "C" int gm_tet_fault(gm_tet* t, const int64_t* pairs, int64_t n_pairs, co
 {
     if (!t) return GM_EINVAL;
     if (!t->has_mesh) return t->set_err(GM_ESTATE, "tet fault: no mesh");
-    if (!pairs || !tris || !t1_ref || !fp || n_pairs < 1 || n_tris < 1 || n_pairs > t->N || n_tris > (1LL << 29))
+    if (!pairs || !tris || !t1_ref || !fp || n_pairs < 1 || n_tris < 1 || n_pairs > t->N || n_tris > (1LL << 27))
         return t->set_err(GM_EINVAL, "tet fault: bad arguments");
     if (!(fp->kn >= 0) || !(fp->ks > 0) || !(fp->f >= 0) || !(fp->w0 > 0) || !(fp->wk_par >= 0) || !(fp->MF > 0))
         return t->set_err(GM_EINVAL, "tet fault: invalid fault parameters");
