@@ -18,7 +18,8 @@ fault terms, solved directly (sparse LU plus two steps of iterative refinement):
 Pinned by: tests/test_oracle_tet.py (symmetry and rigid modes; exact strain
 energy, Biot work, storage energy against an independent quadrature and Darcy
 energy of linear fields; assembled patch identities and the surface-load
-resultant on the Cryer octant; Cryer's centre pressure within the paper's 4 %).
+resultant on the Cryer octant; 1-D consolidation on a tetrahedral column at
+second order; Cryer's centre pressure within the paper's 4 %).
 """
 from __future__ import annotations
 

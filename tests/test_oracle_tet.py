@@ -135,3 +135,27 @@ def test_tet_assembled_patch_identities():
     fx = m.fu.reshape(3, m.N)[0].sum()
     assert fx == pytest.approx(-prob.sigma0 * area_x0, rel=1e-12)
     assert area_x0 == pytest.approx(np.pi / 4, rel=0.05)          # quarter disc of radius 1
+
+
+def terzaghi_tet_error(nz, steps=400, tstar=0.2):
+    H, F = 1.0, 1e6
+    p0, cv = A.terzaghi_params(E, NU, ALPHA, M, K, MU, F)
+    t_end = tstar * H * H / cv
+    prob = W.column_terzaghi_tet(nz=nz, H=H, load=F, steps=steps, dt=t_end / steps)
+    _, _, _, _, p = tet.run(prob)
+    axis = (prob.nodes[:, 0] == 0) & (prob.nodes[:, 1] == 0)
+    err = np.abs(p[axis] - A.terzaghi_pressure(prob.nodes[axis, 2], t_end, H, p0, cv)).max() / p0
+    level = np.round(prob.nodes[:, 2] * nz / H).astype(int)
+    spread = max(np.ptp(p[level == lv]) for lv in range(nz + 1)) / p0
+    return err, spread
+
+
+def test_terzaghi_on_tetrahedra_converges_at_second_order():
+    """1-D consolidation (the series of the structured pin) on a column of
+    Kuhn tetrahedra: the pressure along the column converges to the series at
+    second order (8 -> 16 cells), and the pressure difference between the four
+    nodes of a level, which the Kuhn cut introduces, vanishes at the same rate."""
+    e8, s8 = terzaghi_tet_error(8)
+    e16, s16 = terzaghi_tet_error(16)
+    assert e16 < 0.005 and e8 / e16 > 2.5
+    assert s8 / s16 > 2.5

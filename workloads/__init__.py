@@ -47,6 +47,7 @@ __all__ = [
     "FaultedTetProblem",
     "tetrahedralize",
     "column_terzaghi",
+    "column_terzaghi_tet",
     "theis_plate",
     "tiny_faulted",
     "random_vectors",
@@ -498,6 +499,44 @@ def column_terzaghi(nz: int = 16, H: float = 1.0, load: float = 1e6, steps: int 
                    E=np.full(nel, E), k=np.full(nel, k), nu=nu, alpha=alpha, M=M,
                    mu_f=mu, fixed=fixed, fu=fu, fp=fp, dts=[dt] * steps,
                    notes="1-D consolidation column")
+
+
+def column_terzaghi_tet(nz: int = 16, H: float = 1.0, load: float = 1e6, steps: int = 200,
+                        dt: float = None, E: float = 20e9, nu: float = 0.25, alpha: float = 0.8,
+                        M: float = 50e9, k: float = 1e-15, mu: float = 1e-3) -> TetProblem:
+    """``column_terzaghi`` on linear tetrahedra: the 1 x 1 x nz column of cubes
+    of side H / nz, each cut into the 6 Kuhn tetrahedra along its (0,0,0)-(1,1,1)
+    diagonal; lateral displacements fixed everywhere, u_z = 0 at the bottom,
+    the top face drained (p = 0) and loaded by the compressive traction
+    ``load`` on its two triangles (outward order), all other faces no-flow."""
+    h = H / nz
+    kk, j, i = np.meshgrid(np.arange(nz + 1), np.arange(2), np.arange(2), indexing="ij")
+    i, j, kk = i.ravel(), j.ravel(), kk.ravel()
+    nodes = np.stack([i * h, j * h, kk * h], axis=1).astype(float)
+    nid = lambda a, b, c: a + 2 * (b + 2 * c)
+    tets = []
+    for c in range(nz):
+        for path in _KUHN_PATHS:
+            v = [0, 0, 0]
+            corners = [nid(0, 0, c)]
+            for ax in path:
+                v[ax] += 1
+                corners.append(nid(v[0], v[1], c + v[2]))
+            tets.append(corners)
+    tets = np.array(tets)
+    a, b, cc, d = (nodes[tets[:, q]] for q in range(4))
+    neg = np.einsum("ij,ij->i", np.cross(b - a, cc - a), d - a) < 0
+    tets[neg, 1], tets[neg, 2] = tets[neg, 2].copy(), tets[neg, 1].copy()
+    N = nodes.shape[0]
+    fixed = np.zeros((4, N), np.uint8)
+    fixed[0:2, :] = 1
+    fixed[2, kk == 0] = 1
+    fixed[3, kk == nz] = 1
+    t0, t1, t2, t3 = nid(0, 0, nz), nid(1, 0, nz), nid(0, 1, nz), nid(1, 1, nz)
+    tris = np.array([[t0, t1, t3], [t0, t3, t2]])
+    return TetProblem(name=f"terzaghi_tet{nz}", nodes=nodes, tets=tets, E=E, nu=nu, alpha=alpha, M=M, k=k,
+                      mu_f=mu, fixed=fixed, load_tris=tris, sigma0=load, dts=[1.0 if dt is None else dt] * steps,
+                      notes="1-D consolidation column on Kuhn tetrahedra")
 
 
 def theis_plate(n: int = 32, nz: int = 2, L: float = 40.0, Q: float = 1e-6,
