@@ -69,3 +69,38 @@ def test_fault_steps_match_oracle(case):
             assert rel(st["dlie"], o.dlie) < 1e-9, f"step {k}"
         assert rep["n_slip"] == int((o.flags == 2).sum())
     assert (res[nsteps - 1].flags == 2).sum() >= 1
+
+
+def test_fault_input_errors_are_reported():
+    """Invalid fault descriptions and out-of-order calls return status codes
+    (GM_EINVAL = -1, GM_ESTATE = -7) through the binding as GMError, before any
+    device work: a node in two pairs, a triangle naming a pair out of range,
+    t1_ref normal to the fault, a step before the fault is set, dt = 0."""
+    need_gpu()
+    import paper_2410_17133_gb300 as gm
+    prob = W.tetrahedralize(W.tiny_faulted(2, 2, 2))
+    s = gm.TetFaultSolver()
+    s.mesh(prob.nodes, prob.tets)
+    s.materials(prob.E[0], prob.nu, prob.alpha, prob.M, prob.k[0], prob.mu_f)
+    u = torch.zeros((3, s.N), dtype=torch.float64, device="cuda")
+    p = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    with pytest.raises(gm.GMError) as e:
+        s.fault_step(1.0, u, p)
+    assert e.value.code == -7
+    bad = prob.pairs.copy()
+    bad[1] = bad[0]
+    with pytest.raises(gm.GMError) as e:
+        s.fault(bad, prob.fault_tris, prob.t1_ref, prob.fault)
+    assert e.value.code == -1
+    tris = prob.fault_tris.copy()
+    tris[0, 0] = prob.pairs.shape[0]
+    with pytest.raises(gm.GMError) as e:
+        s.fault(prob.pairs, tris, prob.t1_ref, prob.fault)
+    assert e.value.code == -1
+    with pytest.raises(gm.GMError) as e:
+        s.fault(prob.pairs, prob.fault_tris, (0.0, 0.0, 1.0), prob.fault)
+    assert e.value.code == -1
+    s.fault(prob.pairs, prob.fault_tris, prob.t1_ref, prob.fault)
+    with pytest.raises(gm.GMError) as e:
+        s.fault_step(0.0, u, p)
+    assert e.value.code == -1
