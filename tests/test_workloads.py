@@ -3,6 +3,7 @@ faulted-aquifer workload projects its in-situ stress on the same fault frame
 (n, t1, t2) that the oracle (and the library) build from the grid, its line
 source injects exactly Q, and its layers are where they are stated."""
 import numpy as np
+import pytest
 
 import workloads as W
 from oracle import fem
@@ -98,3 +99,29 @@ def test_stress_rotation_matches_the_papers_orientation_statements():
     assert np.allclose(-np.sum(tr * fg["n"], 1), p.fault.tn0, rtol=1e-12)
     assert np.allclose(np.sum(tr * fg["t1"], 1), p.fault.tau0[:, 0], rtol=1e-10, atol=1e-6)
     assert np.allclose(np.sum(tr * fg["t2"], 1), p.fault.tau0[:, 1], rtol=1e-10, atol=1e-6)
+
+
+def test_tetrahedralized_box_is_conforming():
+    """Kuhn tetrahedralisation of a sheared faulted box: positive volumes that
+    sum to the box volume; every fault triangle is a face of exactly one
+    tetrahedron on each lip (interior faces are shared by two, so the fault
+    surface is the only internal boundary); no tetrahedron holds both lips of
+    a pair (the tetrahedral fault kernels rely on it)."""
+    base = W.tiny_faulted(3, 2, 4, shear=(0.3, 0.2), h=(0.5, 0.4, 0.25))
+    p = W.tetrahedralize(base)
+    a, b, c, d = (p.nodes[p.tets[:, q]] for q in range(4))
+    vol = np.einsum("ij,ij->i", np.cross(b - a, c - a), d - a) / 6.0
+    assert vol.min() > 0
+    assert vol.sum() == pytest.approx(1.5 * 0.8 * 1.0, rel=1e-12)
+    faces = {}
+    for t in p.tets:
+        for f in ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3)):
+            key = tuple(sorted(t[list(f)]))
+            faces[key] = faces.get(key, 0) + 1
+    for lip in (0, 1):
+        assert all(faces.get(tuple(sorted(p.pairs[tri, lip])), 0) == 1 for tri in p.fault_tris)
+    boundary = [k for k, v in faces.items() if v == 1]
+    n_outer = 2 * (2 * (3 * 2 + 3 * 4 + 2 * 4))          # two triangles per outer quad face
+    assert len(boundary) == n_outer + 2 * len(p.fault_tris)
+    lipm, lipp = set(p.pairs[:, 0]), set(p.pairs[:, 1])
+    assert not any(lipm & set(t) and lipp & set(t) for t in p.tets)
