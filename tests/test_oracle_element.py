@@ -165,3 +165,40 @@ def test_fault_coupling_identities():
     u[:, fg["pairs"][:, 1]] = 1e-5 * n[:, None]
     q = model.Apu.T @ u.reshape(-1)
     assert q.sum() == pytest.approx(1e-5 * area, rel=1e-12)
+
+
+@pytest.mark.parametrize("shear", [(0.0, 0.0), (1.7320508075688772, 0.0), (0.4, -0.3)])
+def test_transverse_fracture_flow_of_a_uniform_lip_jump(shear):
+    """Transverse fracture flow (Sec. 3.2.3): with p = dp on every node above
+    the fault (the plus lip included) and 0 below, the bulk blocks are
+    constant on each side and <p> is uniform, so only the transverse term
+    k_perp / (mu w0) [[p]] carries flux.  Each plus-lip row must hold
+    A_i k_perp dp / (mu w0), with A_i the nodal share of the sheared quads
+    (hx hy sqrt(1 + sx^2 + sy^2) per quad, a quarter per corner), each
+    minus-lip row its negative, every other row zero, and the plus-lip total
+    must equal the fault plane's area times k_perp dp / (mu w0)."""
+    nx, ny, nz = 3, 4, 2
+    h = (0.5, 0.25, 0.4)
+    prob = W.tiny_faulted(nx, ny, nz, shear=shear, k_perp=3e-13, h=h)
+    model = fem.Model(prob)
+    m = model.mesh
+    fp = prob.fault
+    dp = 2.5e5
+    kk = np.arange(m.N) // m.nb
+    p = np.where(kk >= m.kf + 1, dp, 0.0)
+    flux = model.C @ p
+    coef = fp.k_perp * dp / (prob.mu_f * fp.w0)
+    quad_area = h[0] * h[1] * np.sqrt(1.0 + shear[0] ** 2 + shear[1] ** 2)
+    i = np.arange(m.nb) % (m.nx + 1)
+    j = np.arange(m.nb) // (m.nx + 1)
+    share = (np.where((i == 0) | (i == m.nx), 0.5, 1.0) * np.where((j == 0) | (j == m.ny), 0.5, 1.0))
+    Ai = quad_area * share
+    plus = m.kf + 1
+    minus = m.kf
+    assert flux[plus * m.nb:(plus + 1) * m.nb] == pytest.approx(Ai * coef, rel=1e-12)
+    assert flux[minus * m.nb:(minus + 1) * m.nb] == pytest.approx(-Ai * coef, rel=1e-12)
+    rest = np.ones(m.N, bool)
+    rest[minus * m.nb:(plus + 1) * m.nb] = False
+    assert np.abs(flux[rest]).max() <= 1e-12 * coef * quad_area
+    total = nx * h[0] * ny * h[1] * np.sqrt(1.0 + shear[0] ** 2 + shear[1] ** 2)
+    assert flux[plus * m.nb:(plus + 1) * m.nb].sum() == pytest.approx(total * coef, rel=1e-12)
