@@ -6,18 +6,21 @@ fault return map, each Jacobian system solved by Prevost's partitioned CG with
 inner PCG solves (every row of the hot path: bulk/fault operator applies, return
 map, residual, preconditioners, CG vector work).
 
-Default workload: the slip-front set-up (Sec. 4.2, Table 1) on 64^3 Q1 hexes,
-40 m cube, horizontal fault at mid-height, tied fault pressures, constant
-centre injection, geometric time steps; Newton to a 1e-8 scaled residual.
-(--config inclined160: 160^3 sheared grid with a 60-degree fault and seeded
-lognormal permeability.)  The headline
-runs the FP32-refined solver (FP32 operators + preconditioners inside the FP64
+Default workload (the configuration the metric is quoted on): 160^3 Q1 hexes
+on a grid sheared so that the fault node plane dips 60 degrees, per-element
+log-normal permeability (log10 k ~ N(-15, 0.5)) and E ~ U[10, 30] GPa from a
+seeded generator, friction 0.6, constant injection at the fault centre, tied
+lip pressures, 5 s steps; Newton to a 1e-8 scaled residual.  The headline runs
+the FP32-refined solver (FP32 operators and preconditioners inside the FP64
 Newton / refinement loop; residuals, dots, return map in FP64); the plain FP64
-solver is timed beside it on the same steps.
+solver runs the first --fp64-steps of the same timed steps from the same state
+and the speed-up compares the two over that identical window.
+(--config slipfront64: the 64^3 slip-front set-up of Sec. 4.2.)
 
 value = mesh DoF x implicit steps / time  (GDoF/s; s per implicit step is
-ms_per_step / 1000).  The operator-apply throughput of the dominant kernel is in
-"roofline" and "apply".
+ms_per_step / 1000).  The operator-apply throughputs (coupled Jacobian, K_T,
+K_b, A22; FP32 and FP64) are in "apply", the dominant kernel's roofline in
+"roofline".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -48,62 +51,64 @@ FP64_PEAK_TFLOPS = 1.25                               # nominal GB300 FP64
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gm", choices=["gm", "reference"])
-    ap.add_argument("--config", default="slipfront64", choices=["inclined160", "slipfront64"])
-    ap.add_argument("--fp64-steps", type=int, default=3,
-                    help="steps of the plain FP64 solver timed beside the headline")
+    ap.add_argument("--config", default="inclined160", choices=["inclined160", "slipfront64"])
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="the first steps of the timed window, run again by the plain FP64 solver")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--apply-profile", type=int, default=0, metavar="N",
-                    help="only run K_T applies (FP32 twice, FP64 twice) on the N^3 slip-front "
-                         "grid, for kernel profiling; prints their times")
+                    help="only run one K_b, K_T, J and A22 apply in FP32 and FP64 on the N^3 grid "
+                         "of the workload, for kernel profiling; prints their times")
     return ap.parse_args()
 
 
-def run_apply_profile(n):
-    """Small fixed sequence of bulk K_T applies (the dominant kernel) for ncu."""
+def run_apply_profile(n, config):
+    """Small fixed sequence of operator applies (the bulk kernels) for ncu:
+    K_b (one bulk launch), K_T, the coupled Jacobian and A22, FP32 then FP64, on
+    the n^3 version of the workload."""
     import torch
 
     import __graft_entry__ as ge
     ge.build()
     import paper_2410_17133_gb300 as gm
-    import workloads as W
-    prob = W.slip_front(n=n)
+    prob = sample_workload(config, n)
     s = gm.Solver.from_problem(prob)
+    s.timestep(prob.dts[0])
     N = s.N
     out = {"nodes": N, "elements": s.n_el}
     for name, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
-        x = (torch.randn(3, N, dtype=torch.float64, device="cuda") * 1e-6).to(dt)
-        y = torch.empty_like(x)
-        ms = []
-        for _ in range(2):
+        for which, shp in (("KB", (3, N)), ("KT", (3, N)), ("J", (4, N)), ("A22", (N,))):
+            x = (torch.randn(shp, dtype=torch.float64, device="cuda") * 1e-6).to(dt)
+            y = torch.empty_like(x)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record()
-            s.apply("KT", x, y)
+            s.apply(which, x, y)
             b.record()
             b.synchronize()
-            ms.append(a.elapsed_time(b))
-        out[name + "_ms"] = ms
+            out[f"{which}_{name}_ms"] = a.elapsed_time(b)
     print(json.dumps(out))
 
 
-def workload(name):
+def workload(name, steps=20):
     import workloads as W
     if name == "inclined160":
-        return W.inclined_lognormal(n=160), {"workload": "inclined-fault 160^3 Q1, lognormal k, E~U[10,30] GPa, 60 deg fault, tied lip pressures",
-                                             "mesh": [160, 160, 160], "seed": 3}
-    return W.slip_front(n=64), {"workload": "slip-front 64^3 Q1 (Table 1 fault, ratio 0.99, T=0.1)", "mesh": [64, 64, 64]}
+        return W.inclined_lognormal(n=160, steps=steps), {
+            "workload": "inclined-fault 160^3 Q1 hexes (16.8 M DoF), 60 deg fault, lognormal k "
+                        "(log10 N(-15, 0.5)), E ~ U[10, 30] GPa, constant injection, 5 s steps",
+            "mesh": [160, 160, 160], "seed": 3}
+    return W.slip_front(n=64, steps=max(steps, 50)), {
+        "workload": "slip-front 64^3 Q1 (Table 1 fault, ratio 0.99, T=0.1)", "mesh": [64, 64, 64]}
 
 
-def sample_workload(name, n):
+def sample_workload(name, n, steps=20):
     """Same physics on a smaller grid: the bounded sample the CPU oracle runs."""
     import workloads as W
     if name == "inclined160":
-        p = W.inclined_lognormal(n=n)
-        return p
-    return W.slip_front(n=n)
+        return W.inclined_lognormal(n=n, steps=steps)
+    return W.slip_front(n=n, steps=max(steps, 50))
 
 
 # ---------------------------------------------------------------------------
@@ -162,22 +167,23 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("gm_bulk.cuh", "gm_apply.cuh"):
+    for f in ("gm_bulk32.cuh", "gm_apply.cuh", "gm_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2410_17133_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def bulk_flops_per_element(cls_nb, mode):
-    """FP operations per element of the parity-basis bulk kernel (FMA = 2).
-    K mode: xy transform 8/field/plane, z stage 8/field, block products
-    nb*bu^2 FMAs + 24 scalings, ob/ot accumulation 2/output, inverse xy 12/field,
-    node gather 3/field."""
-    bu = 24 // cls_nb
-    if mode == "K":
-        nf = 3
-        return nf * 8 + nf * 8 + 2 * cls_nb * bu * bu + 24 + 2 * 24 + nf * 12 + nf * 3
-    raise ValueError(mode)
+# entries of the parity-basis elasticity operator multiplied per element (the
+# cell pattern of gm_make_parpat): box, cell sheared in x-z, general cell
+K_PATTERN = {0: 45, 1: 73, 2: 109}
+
+
+def bulk_flops_per_element(cls):
+    """FP32 operations per element of the K_b bulk kernel (FMA = 2): xy
+    transform 7 per field (the shared row is transformed once for two faces), z
+    transform 21, pattern products 2 x nnz, inverse z with the element scale 42,
+    inverse xy and node sums 11 per field."""
+    return 3 * 7 + 21 + 2 * K_PATTERN[cls] + 42 + 3 * 11
 
 
 def log(*a):
@@ -219,7 +225,9 @@ def run_gm(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize()
 
-    prob, cfg = workload(args.config)
+    W, K, F = args.warmup, args.steps, min(args.fp64_steps, args.steps)
+    KE = min(K, 2)
+    prob, cfg = workload(args.config, steps=W + K + KE + 4)
     s = gm.Solver.from_problem(prob, device=local_rank)
     N = s.N
     ndof = 4 * N
@@ -245,11 +253,10 @@ def run_gm(args, rank, world, local_rank):
         return ms, reps
 
     # warm-up (FP32-refined headline solver)
-    W, K = args.warmup, args.steps
     timed_steps(s, range(W), gm.F32)
     log("warm-up done")
     a_w = s.get_state()
-    l0, _ = s.counters()
+    l0, ap0 = s.counters()
     with ClockSampler(local_rank) as clk:
         barrier()
         t_wall0 = time.perf_counter()
@@ -258,70 +265,86 @@ def run_gm(args, rank, world, local_rank):
         torch.cuda.nvtx.range_pop()
         t_wall = time.perf_counter() - t_wall0
     clocks = clk.summary()
-    l1, _ = s.counters()
+    l1, ap1 = s.counters()
     launches = l1 - l0
     log("timed steps", ms)
     total_ms = max_over_ranks(sum(ms), dist, "cuda")
     value = whole_job_value(ndof, K, world, total_ms)
 
-    # plain FP64 solver on the same steps (fresh state advanced by the same warm-up)
+    # plain FP64 solver on the first F timed steps, from the same warmed-up state
     fp64 = None
-    if args.fp64_steps > 0:
-        # the FP64 solver starts from the warmed-up state and runs the same steps
-        a = a_w
+    if F > 0:
         s64 = gm.Solver.from_problem(prob, device=local_rank)
-        s64.set_state(u=a["u"], p=a["p"], dlie=a["dlie"], flags=a["flags"])
-        m64, r64 = timed_steps(s64, range(W, W + args.fp64_steps), gm.F64)
+        s64.set_state(u=a_w["u"], p=a_w["p"], dlie=a_w["dlie"], flags=a_w["flags"])
+        m64, r64 = timed_steps(s64, range(W, W + F), gm.F64)
         log("fp64 steps", m64)
         b64 = s64.get_state()
-        # agreement of the two solvers after the same step (both converged to 1e-8)
+        del s64
+        # the FP32-refined solver over the same steps from the same state, for
+        # the agreement of the two converged solutions
         s_chk = gm.Solver.from_problem(prob, device=local_rank)
-        s_chk.set_state(u=a["u"], p=a["p"], dlie=a["dlie"], flags=a["flags"])
-        timed_steps(s_chk, range(W, W + args.fp64_steps), gm.F32)
+        s_chk.set_state(u=a_w["u"], p=a_w["p"], dlie=a_w["dlie"], flags=a_w["flags"])
+        timed_steps(s_chk, range(W, W + F), gm.F32)
         c32 = s_chk.get_state()
+        del s_chk
         du = float(np.linalg.norm(c32["u"] - b64["u"]) / max(np.linalg.norm(b64["u"]), 1e-300))
         dp = float(np.linalg.norm(c32["p"] - b64["p"]) / max(np.linalg.norm(b64["p"]), 1e-300))
-        fp64 = {"ms_per_step": sum(m64) / len(m64), "steps": args.fp64_steps,
-                "value": ndof * len(m64) / (sum(m64) * 1e-3) / 1e9,
-                "speedup_fp32_refined": (sum(m64) / len(m64)) / (total_ms / K),
+        ms32_same = sum(ms[:F]) / F
+        fp64 = {"ms_per_step": sum(m64) / F, "steps": f"{W}..{W + F - 1} (the first {F} of the timed steps)",
+                "value": ndof * F / (sum(m64) * 1e-3) / 1e9,
+                "fp32_refined_ms_per_step_same_steps": ms32_same,
+                "speedup_fp32_refined": (sum(m64) / F) / ms32_same,
                 "newton": [r["newton"] for r in r64], "inner_k": [r["inner_k"] for r in r64],
+                "inner_a": [r["inner_a"] for r in r64],
                 "rel_l2_u_vs_fp32_refined": du, "rel_l2_p_vs_fp32_refined": dp,
-                "flags_equal": bool(np.array_equal(c32["flags"], b64["flags"]))}
-        del s64, s_chk
+                "flags_equal": bool(np.array_equal(c32["flags"], b64["flags"])),
+                "preconditioners": "same as the FP32-refined solver (multigrid K_T, Jacobi A22), in FP64"}
 
-    # dominant kernel: bulk K_T apply in the inner PCG (FP32 for the headline)
-    x32 = torch.randn(3, N, dtype=torch.float32, device="cuda") * 1e-6
-    y32 = torch.empty_like(x32)
-    x64 = x32.double()
-    y64 = torch.empty_like(x64)
-
-    def apply_time(x, y, reps=20):
-        s.apply("KT", x, y, stream=stream)
+    # operator applies: median of 20 launches each, L2 flushed between them
+    def apply_time(which, x, y, reps=20):
+        s.apply(which, x, y, stream=stream)
         ts = []
         for _ in range(reps):
             flush.fill_(1.0)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            s.apply("KT", x, y, stream=stream)
+            s.apply(which, x, y, stream=stream)
             b.record(stream)
             b.synchronize()
             ts.append(a.elapsed_time(b))
-        return statistics.mean(ts)
+        return statistics.median(ts) * 1e-3
 
     log("applies")
-    t32 = apply_time(x32, y32) * 1e-3
-    t64 = apply_time(x64, y64) * 1e-3
-    nb = 8 if prob.shear == (0.0, 0.0) else (4 if prob.shear[1] == 0.0 else 2)
+    s.timestep(prob.dts[W])
+    apply = {}
+    t_app = {}
+    for which, nf in (("KB", 3), ("KT", 3), ("J", 4), ("A22", 1)):
+        for tag, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+            shp = (nf, N) if nf > 1 else (N,)
+            x = (torch.randn(shp, dtype=torch.float64, device="cuda") * 1e-6).to(dt)
+            y = torch.empty_like(x)
+            t = apply_time(which, x, y)
+            t_app[(which, tag)] = t
+            apply[f"{which}_{tag}_us"] = t * 1e6
+            apply[f"{which}_{tag}_gdofs"] = nf * N / t / 1e9
+    cls = 0 if prob.shear == (0.0, 0.0) else (1 if prob.shear[1] == 0.0 else 2)
     n_el = s.n_el
-    flops = bulk_flops_per_element(nb, "K") * n_el
-    bytes32 = 28.0 * N            # u read + y write (3 x 4 B each) + E (4 B) per node
+    t32 = t_app[("KB", "fp32")]
+    flops = bulk_flops_per_element(cls) * n_el
+    bytes32 = 28.0 * N            # u read + y write (3 x 4 B each) + E (4 B per element ~ per node)
+    apply["J_fp32_GBs_40B_per_node"] = 40.0 * N / t_app[("J", "fp32")] / 1e9
+    apply["J_fp64_GBs_80B_per_node"] = 80.0 * N / t_app[("J", "fp64")] / 1e9
+    apply["KB_fp64_alu_frac_nominal"] = flops / t_app[("KB", "fp64")] / 1e12 / FP64_PEAK_TFLOPS
+    apply["notes"] = ("KB: bulk kernel alone (one launch); KT adds the fault kernel; J: the coupled "
+                      "Jacobian (4 DoF per node; FP32 and FP64 run the generic coupled bulk kernel); "
+                      "GDoF/s = field DoF of the product / launch time")
     peaks = {}
     if os.path.exists(PEAKS_FILE):
         with open(PEAKS_FILE) as fh:
             peaks = json.load(fh)
     hbm_peak = peaks.get("hbm_gbs", FALLBACK_HBM)
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
     traffic = None
     if os.path.exists(TRAFFIC_FILE):
         with open(TRAFFIC_FILE) as fh:
@@ -330,62 +353,52 @@ def run_gm(args, rank, world, local_rank):
             traffic = tr.get("dram_bytes_per_launch")
     ach_gbs = bytes32 / t32 / 1e9
     ach_tf = flops / t32 / 1e12
-    frac_hbm = ach_gbs / hbm_peak
-    frac_alu = ach_tf / FP32_PEAK_TFLOPS
-    if frac_hbm >= frac_alu:
-        roof = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": frac_hbm, "traffic": traffic, "peak_source": peak_src,
-                "alt_alu": {"achieved": ach_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": frac_alu}}
-    else:
-        roof = {"bound": "alu", "achieved": ach_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": frac_alu, "traffic": traffic, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                "alt_hbm": {"achieved": ach_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": frac_hbm}}
-    roof["kernel"] = "gm_bulk_apply_kernel<float,K> (+ fault kernel): the K_T product on the finest grid, the largest per-launch cost; the multigrid smoother, summed over all grid levels, has the larger share of launches"
-    roof["launch_ms"] = t32 * 1e3
-    apply = {"KT_fp32_gdofs": 3 * N / t32 / 1e9, "KT_fp64_gdofs": 3 * N / t64 / 1e9,
-             "KT_fp32_ms": t32 * 1e3, "KT_fp64_ms": t64 * 1e3,
-             "KT_fp64_alu_frac": flops / t64 / 1e12 / FP64_PEAK_TFLOPS,
-             "fp64_peak_tflops_nominal": FP64_PEAK_TFLOPS}
+    roof = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm_peak, "unit": "GB/s",
+            "frac": ach_gbs / hbm_peak, "traffic": traffic, "peak_source": peak_src,
+            "alt_alu": {"achieved": ach_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": ach_tf / FP32_PEAK_TFLOPS,
+                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+            "kernel": "gm_bulk32_kernel (K_b, FP32): the bulk elasticity product of the inner K_T "
+                      "solves and the multigrid smoother",
+            "bytes_per_launch": bytes32, "launch_us": t32 * 1e6}
 
-    # end to end through the public API with host buffers: upload state, step,
-    # download state + flags every step
-    e2e = None
-    if True:
+    # end to end through the public API with host buffers: each step uploads
+    # the state from pinned host memory, steps, downloads state and flags
+    a = s.get_state()
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in a.items()}
+    h2d = sum(pin[k].numel() * pin[k].element_size() for k in ("u", "p", "dlie", "flags"))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(W + K, W + K + KE):
+        s.set_state(u=pin["u"].numpy(), p=pin["p"].numpy(), dlie=pin["dlie"].numpy(), flags=pin["flags"].numpy())
+        s.step(prob.dts[k], newton_rtol=NEWTON_RTOL, precision=gm.F32, stream=stream)
         a = s.get_state()
-        h2d = a["u"].nbytes + a["p"].nbytes + a["dlie"].nbytes + a["flags"].nbytes
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ke = 0
-        for k in range(W + K, W + 2 * K):
-            s.set_state(u=a["u"], p=a["p"], dlie=a["dlie"], flags=a["flags"])
-            s.step(prob.dts[k], newton_rtol=NEWTON_RTOL, precision=gm.F32, stream=stream)
-            a = s.get_state()
-            ke += 1
-        torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        d2h = a["u"].nbytes + a["p"].nbytes + a["slip"].nbytes + a["dlie"].nbytes + a["flags"].nbytes
-        e2e = {"value": ndof * ke * world / te / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": te / ke * 1e3}
-
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    d2h = sum(a[k].nbytes for k in ("u", "p", "slip", "dlie", "flags"))
+    e2e = {"value": ndof * KE * world / te / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h), "ms_per_step": te / KE * 1e3, "steps": KE}
     log("e2e done")
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.config, budget_s=20.0)
+        cpu = cpu_baseline(args.config)
 
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32-refined(f64 residual/dots/return map)",
+            "vs_baseline": None, "dtype": "f32-refined (f32 operators/preconditioners; f64 residual, dots, return map)",
             "data": "synthetic (seeded workload restating the paper's set-up; no paper meshes)",
             "config": dict(cfg, dofs=ndof, newton_rtol=NEWTON_RTOL,
                            steps_timed=f"{W}..{W + K - 1} of the schedule",
                            l2="flushed (512 MB write) between timed steps and between timed applies",
-                           inner_solvers="FP32 K_T: PCG with a multigrid V-cycle; A22: Jacobi PCG; "
-                                         "FP64 comparison: PCG with nodal/lip-pair block Jacobi",
+                           inner_solvers="K_T: PCG with a geometric multigrid V-cycle; A22: Jacobi PCG; "
+                                         "the FP64 comparison uses the same preconditioners in FP64",
                            parallelism=f"replicas{world}" if world > 1 else "single"),
             "roofline": roof, "apply": apply, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "gpu_launches": int(launches),
+            "launches_per_step": launches / K, "bulk_applies_per_step": (ap1 - ap0) / K,
             "per_step": [{"ms": m, "newton": r["newton"], "outer": r["outer"], "inner_k": r["inner_k"],
                           "inner_a": r["inner_a"], "slip": r["n_slip"], "open": r["n_open"]}
                          for m, r in zip(ms, reps)],
@@ -403,7 +416,7 @@ def run_gm(args, rank, world, local_rank):
 def oracle_steps(config, n, steps):
     from oracle import solve as osolve
     from oracle.fem import Model
-    prob = sample_workload(config, n)
+    prob = sample_workload(config, n, steps=max(steps, 20))
     model = Model(prob)
     st = osolve.initial_state(model)
     times = []
@@ -414,13 +427,55 @@ def oracle_steps(config, n, steps):
     return 4 * model.N, times
 
 
-def cpu_baseline(config, budget_s=20.0):
-    n = 12
-    ndof, times = oracle_steps(config, n, 2)
-    return {"value": ndof * len(times) / sum(times) / 1e9, "unit": "GDoF/s", "cores": 1,
-            "kind": "oracle",
-            "sample": f"first {len(times)} implicit steps of the same workload on a {n}^3 grid "
-                      f"({ndof} DoF), scipy SuperLU direct solves (single thread), {sum(times):.1f} s"}
+def oracle_spmv(config, n, reps=5):
+    """The oracle's assembled coupled Jacobian [K_b, -A_pu; A_up, S + dt C] (CSR)
+    times a vector, on one thread and on all host cores (row blocks on threads:
+    scipy's CSR product releases the GIL).  Returns GDoF/s both ways."""
+    import numpy as np
+    import scipy.sparse as sp
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle.fem import Model
+    prob = sample_workload(config, n)
+    m = Model(prob)
+    J = sp.bmat([[m.Kb, -m.Apu], [m.Apu.T, m.A22(prob.dts[0])]]).tocsr()
+    x = np.random.default_rng(0).standard_normal(J.shape[1])
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        y1 = J @ x
+    t1 = (time.perf_counter() - t0) / reps
+    nt = os.cpu_count() or 1
+    cut = np.linspace(0, J.shape[0], nt + 1).astype(int)
+    parts = [J[cut[i]:cut[i + 1]] for i in range(nt)]
+    y = np.empty(J.shape[0])
+
+    def work(i):
+        y[cut[i]:cut[i + 1]] = parts[i] @ x
+
+    with ThreadPoolExecutor(nt) as ex:
+        list(ex.map(work, range(nt)))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            list(ex.map(work, range(nt)))
+        tn = (time.perf_counter() - t0) / reps
+    assert np.allclose(y, y1)
+    return J.shape[0], J.nnz, J.shape[0] / t1 / 1e9, J.shape[0] / tn / 1e9, nt
+
+
+def cpu_baseline(config, n_step=12, n_spmv=32):
+    """The oracle on the machine's host cores, bounded: implicit steps of the same
+    workload on an n_step^3 grid (sparse direct solves, one thread) and its
+    assembled coupled-Jacobian SpMV on an n_spmv^3 grid (one thread and all
+    cores)."""
+    ndof, times = oracle_steps(config, n_step, 2)
+    nrow, nnz, g1, gn, nt = oracle_spmv(config, n_spmv)
+    return {"value": ndof * len(times) / sum(times) / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {len(times)} implicit steps of the same workload on a {n_step}^3 grid "
+                      f"({ndof} DoF; scipy SuperLU direct solves, one thread), {sum(times):.1f} s",
+            "s_per_step": sum(times) / len(times),
+            "spmv_gdofs_all_cores": gn, "spmv_cores": nt, "spmv_gdofs_1_core": g1,
+            "spmv_sample": f"assembled coupled Jacobian of the same workload on a {n_spmv}^3 grid "
+                           f"({nrow} rows, {nnz} nonzeros, FP64 CSR), y = J x; all cores = row blocks "
+                           f"on {nt} threads"}
 
 
 def run_reference(args, rank, world):
@@ -448,7 +503,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.apply_profile:
-        run_apply_profile(args.apply_profile)
+        run_apply_profile(args.apply_profile, args.config)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

@@ -210,8 +210,11 @@ int gm_residual(gm_ctx* ctx, const double* du_dev, const double* dp_dev, double*
  * gm_residual keeps in the context lives instead in one library-owned device
  * array of about 1 MB (held on every GPU that loads the library until the
  * process exits), so the call allocates nothing.  Limit: at most 16,777,216
- * nodes; larger problems get GM_EINVAL.  The first call on a device looks up
- * the array's device address; make that first call before any stream capture.
+ * nodes; larger problems get GM_EINVAL before any GPU work.  Every call looks
+ * up the array's device address with the context's device current (the lookup
+ * allocates nothing, and a context re-created after cudaDeviceReset gets the
+ * new address); the first lookup on a device may load the library's device
+ * code, so make the first call on a device before any stream capture.
  * All calls share the array and it keeps the last call's contents: calls whose
  * GPU work overlaps (other streams or contexts on the same device) race and
  * must be serialised by the caller.  Synchronises. */

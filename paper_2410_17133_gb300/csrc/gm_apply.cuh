@@ -18,7 +18,11 @@
 // block sums all partials in a fixed order and forms alpha = (r.z)/(p.Ap).
 #pragma once
 
+#include <algorithm>
+#include <type_traits>
+
 #include "gm_bulk.cuh"
+#include "gm_bulk32.cuh"
 
 __device__ inline void gm_pcg_alpha_from(PcgScalars* sc, double pq)
 {
@@ -231,6 +235,76 @@ inline void gm_bulk_geometry(const gm_ctx* c, int* gx, int* gy, int* gz, int* zc
     *gz = (c->g.nplanes + zc - 1) / zc;
 }
 
+// Plane-chunk length of a bulk launch: the chunk count is chosen so that the
+// CTAs fill whole waves of the resident slots, each CTA's march costing its
+// planes plus the halo layer and the pipeline fill.
+inline int gm_pick_zchunk(const gm_ctx* c, long long xy, int resident)
+{
+    const int np = c->g.nplanes;
+    if (c->zchunk_override > 0) return std::max(2, c->zchunk_override);
+    const long long slots = (long long)c->sm_count * std::max(resident, 1);
+    int best = np;
+    long long bestc = -1;
+    for (int zc = 2; zc <= np; ++zc) {
+        const long long chunks = (np + zc - 1) / zc;
+        const long long waves = (xy * chunks + slots - 1) / slots;
+        const long long cost = waves * (zc + 3);
+        if (bestc < 0 || cost < bestc) { bestc = cost; best = zc; }
+    }
+    return best;
+}
+
+// FP32 bulk kernel (gm_bulk32.cuh): dynamic shared memory opt-in and resident
+// CTAs per SM, set once per device (at bind, outside any stream capture).
+template <int CLS, int MODE, bool PCG>
+static int& gm_bulk32_resident(int dev)
+{
+    static int resident[64] = {};
+    return resident[dev & 63];
+}
+
+template <int CLS, int MODE, bool PCG>
+static int gm_bulk32_setup(int dev)
+{
+    constexpr size_t SMEM = gm32::smem_bytes<MODE, PCG>();
+    int& r = gm_bulk32_resident<CLS, MODE, PCG>(dev);
+    if (r > 0) return 0;
+    cudaError_t e = cudaFuncSetAttribute(gm_bulk32_kernel<CLS, MODE, PCG>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    if (e != cudaSuccess) return (int)e;
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gm_bulk32_kernel<CLS, MODE, PCG>, gm32::NT, SMEM);
+    if (e != cudaSuccess) return (int)e;
+    r = std::max(n, 1);
+    return 0;
+}
+
+// Launch; returns the number of CTAs.
+template <int CLS, int MODE, bool PCG>
+static int gm_bulk32_launch(gm_ctx* c, BulkArgs<float>& b, cudaStream_t s)
+{
+    constexpr size_t SMEM = gm32::smem_bytes<MODE, PCG>();
+    const int dev = c->device;
+    gm_bulk32_setup<CLS, MODE, PCG>(dev);
+    const int resident = gm_bulk32_resident<CLS, MODE, PCG>(dev);
+    const int gx = (c->nx + 1 + 14) / 15, gy = (c->ny + 1 + 14) / 15;
+    const int zc = gm_pick_zchunk(c, (long long)gx * gy, resident);
+    const int gz = (c->g.nplanes + zc - 1) / zc;
+    b.zchunk = zc;
+    gm_bulk32_kernel<CLS, MODE, PCG><<<dim3(gx, gy, gz), gm32::NT, SMEM, s>>>(b, c->R32p);
+    return gx * gy * gz;
+}
+
+template <int MODE, bool PCG>
+static int gm_bulk32_dispatch(gm_ctx* c, BulkArgs<float>& b, cudaStream_t s)
+{
+    switch (c->cls) {
+    case GM_CLS_BOX: return gm_bulk32_launch<GM_CLS_BOX, MODE, PCG>(c, b, s);
+    case GM_CLS_MONO: return gm_bulk32_launch<GM_CLS_MONO, MODE, PCG>(c, b, s);
+    default: return gm_bulk32_launch<GM_CLS_GEN, MODE, PCG>(c, b, s);
+    }
+}
+
 template <typename T>
 inline FaultArgs<T> gm_fault_args(gm_ctx* c, double cK, double cApu, double cAup, double cS, double cC,
                                   bool kf_on)
@@ -292,10 +366,15 @@ static void gm_apply_launch_t(gm_ctx* c, const RefOps<T>& R, double cK, double c
     b.xu = xu; b.xp = xp; b.yu = yu; b.yp = yp;
     b.skip = skip;
     constexpr int BULK = MODE & (GM_M_K | GM_M_APU | GM_M_AUP | GM_M_S | GM_M_C);
-    gm_bulk_apply_kernel<T, CLS, BULK, false><<<dim3(gx, gy, gz), 256, 0, s>>>(b, R);
+    if constexpr (std::is_same<T, float>::value && (BULK == GM_M_K || BULK == (GM_M_S | GM_M_C)))
+        gm_bulk32_launch<CLS, BULK, false>(c, b, s);
+    else
+        gm_bulk_apply_kernel<T, CLS, BULK, false><<<dim3(gx, gy, gz), 256, 0, s>>>(b, R);
     c->applies++;
     c->launches++;
-    if (c->g.kf >= 0) {
+    // K_b alone has no fault term: the bulk kernel's product is complete
+    constexpr bool FAULT_TERMS = (MODE & (GM_M_KF | GM_M_APU | GM_M_AUP | GM_M_S | GM_M_C)) != 0;
+    if (FAULT_TERMS && c->g.kf >= 0) {
         FaultArgs<T> f = gm_fault_args<T>(c, cK, cApu, cAup, cS, cC, (MODE & GM_M_KF) != 0);
         f.xu = xu; f.xp = xp; f.yu = yu; f.yp = yp;
         f.D = D;
@@ -335,7 +414,7 @@ static void gm_pcg_apply_t(gm_ctx* c, const RefOps<T>& R, const T* z, const T* p
     const double cK = U ? 1.0 : 0.0, cS = U ? 0.0 : 1.0, cC = U ? 0.0 : c->dt;
     int gx, gy, gz, zchunk;
     gm_bulk_geometry(c, &gx, &gy, &gz, &zchunk);
-    const int nbulk = gx * gy * gz;
+    int nbulk = gx * gy * gz;
     double* part = c->dpart.as<double>();
     BulkArgs<T> b = gm_bulk_args<T>(c, cK, 0, 0, cS, cC, E, kap);
     b.zchunk = zchunk;
@@ -347,7 +426,10 @@ static void gm_pcg_apply_t(gm_ctx* c, const RefOps<T>& R, const T* z, const T* p
     if (U) { b.xu = p_old; b.zu = z; b.pu_new = p_new; b.yu = q; b.xp = nullptr; b.yp = nullptr; }
     else { b.xp = p_old; b.zp = z; b.pp_new = p_new; b.yp = q; b.xu = nullptr; b.yu = nullptr; }
     constexpr int BULK = MODE & (GM_M_K | GM_M_S | GM_M_C);
-    gm_bulk_apply_kernel<T, CLS, BULK, true><<<dim3(gx, gy, gz), 256, 0, s>>>(b, R);
+    if constexpr (std::is_same<T, float>::value)
+        nbulk = gm_bulk32_launch<CLS, BULK, true>(c, b, s);
+    else
+        gm_bulk_apply_kernel<T, CLS, BULK, true><<<dim3(gx, gy, gz), 256, 0, s>>>(b, R);
     c->applies++;
     c->launches++;
     if (c->g.kf >= 0) {

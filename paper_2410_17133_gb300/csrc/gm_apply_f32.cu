@@ -55,13 +55,29 @@ int gm_launch_bulk_k_f32(gm_ctx* c, const float* x, float* y, cudaStream_t s, co
     b.zchunk = zchunk;
     b.xu = x; b.xp = nullptr; b.yu = y; b.yp = nullptr;
     b.skip = skip;
-    const dim3 grid(gx, gy, gz);
-    switch (c->cls) {
-    case GM_CLS_BOX: gm_bulk_apply_kernel<float, GM_CLS_BOX, GM_M_K, false><<<grid, 256, 0, s>>>(b, c->R32); break;
-    case GM_CLS_MONO: gm_bulk_apply_kernel<float, GM_CLS_MONO, GM_M_K, false><<<grid, 256, 0, s>>>(b, c->R32); break;
-    default: gm_bulk_apply_kernel<float, GM_CLS_GEN, GM_M_K, false><<<grid, 256, 0, s>>>(b, c->R32); break;
-    }
+    gm_bulk32_dispatch<GM_M_K, false>(c, b, s);
     c->applies++;
     GM_LAUNCHED(c);
+    return GM_OK;
+}
+
+// Kernel attributes of the FP32 bulk kernels of the context's cell class (called
+// at bind, so no attribute call happens inside a later stream capture).
+template <int CLS>
+static int gm_bulk32_setup_cls(int dev)
+{
+    int e = gm_bulk32_setup<CLS, GM_M_K, false>(dev);
+    if (!e) e = gm_bulk32_setup<CLS, GM_M_K, true>(dev);
+    if (!e) e = gm_bulk32_setup<CLS, GM_M_S | GM_M_C, false>(dev);
+    if (!e) e = gm_bulk32_setup<CLS, GM_M_S | GM_M_C, true>(dev);
+    return e;
+}
+
+int gm_prepare_bulk32(gm_ctx* c)
+{
+    const int e = c->cls == GM_CLS_BOX ? gm_bulk32_setup_cls<GM_CLS_BOX>(c->device)
+                : c->cls == GM_CLS_MONO ? gm_bulk32_setup_cls<GM_CLS_MONO>(c->device)
+                                        : gm_bulk32_setup_cls<GM_CLS_GEN>(c->device);
+    if (e) return c->set_err(GM_ECUDA, std::string("bulk kernel set-up: ") + cudaGetErrorString((cudaError_t)e));
     return GM_OK;
 }

@@ -8,8 +8,8 @@
 // parallelepiped, so the element matrices are those of one reference cell
 // scaled by the element's E and k.  In the parity basis of the cell (the 8-point
 // Walsh-Hadamard transform of the nodal values, one per field) the reference
-// operators are block-diagonal by the cell's reflection symmetry; the kernel
-// transforms, multiplies block by block and transforms back.
+// operators are sparse (gm_make_parpat); the kernel transforms, multiplies the
+// allowed entries and transforms back.
 //
 // Work decomposition: a CTA of 16x16 threads owns 15x15 node columns and a
 // chunk of node planes; it marches up the planes.  Thread (tx, ty) handles the
@@ -61,8 +61,7 @@ gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
     constexpr int NO = (OUT_U ? 3 : 0) + (OUT_P ? 1 : 0);
     constexpr int IPI = IN_U ? 3 : 0;   // slot of p among the input fields
     constexpr int OPI = OUT_U ? 3 : 0;  // slot of p among the output fields
-    constexpr SecTab ST = gm_make_sectab(CLS);
-    constexpr int NB = ST.nb, BU = ST.bu, BP = ST.bp;
+    constexpr ParPat PP = gm_make_parpat(CLS);
     static_assert(!PCG || (NI == NO && (NI == 3 || NI == 1)), "PCG mode needs a square single-field-group operator");
 
     if (a.skip != nullptr && *a.skip != 0) return;
@@ -157,84 +156,89 @@ gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
         }
     };
 
-    // One element: z part of the transform, sector products, inverse z part.
-    // ob/ot receive the xy-parity tuples of the bottom / top node sets.
+    // One element: z part of the transform, products with the allowed entries
+    // of the parity-basis operators, inverse z part.  ob receives the
+    // xy-parity tuples of the bottom node set (added), ot those of the top set.
     auto element = [&](const T (&tb)[NI][4], const T (&tt)[NI][4], int kb, T (&ob)[NO][4],
                        T (&ot)[NO][4]) {
-#pragma unroll
-        for (int f = 0; f < NO; ++f)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) { ob[f][q] = T(0); ot[f][q] = T(0); }
         const long long e = fi + (long long)g.nx * (fj + (long long)g.ny * layer_index(kb));
         T kE = T(0), kC = T(0), kS = T(0);
         if constexpr (DO_K) kE = a.cK * a.E[e];
         if constexpr (DO_C) kC = a.cC * a.kap[e];
         if constexpr (DO_S) kS = a.fs != nullptr ? a.cS + a.cFS * a.fs[e] : a.cS;
+        // parity values x[f][s] = tb[f][s & 3] +- tt[f][s & 3]
+        T xu[3][8], xp[8];
+        if constexpr (IN_U) {
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            T xu[BU > 0 ? BU : 1];
-            T xp[BP > 0 ? BP : 1];
-            if constexpr (IN_U) {
+            for (int c = 0; c < 3; ++c)
 #pragma unroll
-                for (int k = 0; k < BU; ++k) {
-                    const int c = ST.uc[b][k], s = ST.us[b][k];
-                    xu[k] = (s & 4) ? (tb[c][s & 3] - tt[c][s & 3]) : (tb[c][s & 3] + tt[c][s & 3]);
+                for (int s = 1; s < 8; ++s)
+                    xu[c][s] = (s & 4) ? (tb[c][s & 3] - tt[c][s & 3]) : (tb[c][s & 3] + tt[c][s & 3]);
+        }
+        if constexpr (IN_P) {
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+                xp[s] = (s & 4) ? (tb[IPI][s & 3] - tt[IPI][s & 3]) : (tb[IPI][s & 3] + tt[IPI][s & 3]);
+        }
+        // output parity value of field f, mode s (the constant displacement mode
+        // carries no force: its row of K and A_pu is empty)
+        auto out_u = [&](int c, int s) -> T {
+            T acc = T(0);
+            if constexpr (DO_K) {
+                T t = T(0);
+#pragma unroll
+                for (int j = 0; j < 24; ++j)
+                    if (PP.k[c * 8 + s][j] >= 0 && (j & 7) != 0) t = fma(R.K[PP.k[c * 8 + s][j]], xu[j >> 3][j & 7], t);
+                acc = kE * t;
+            }
+            if constexpr (DO_APU) {
+                T t = T(0);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (PP.a[c * 8 + s][j] >= 0) t = fma(R.A[PP.a[c * 8 + s][j]], xp[j], t);
+                acc = fma(a.cApu, t, acc);
+            }
+            return acc;
+        };
+        auto out_p = [&](int s) -> T {
+            T acc = T(0);
+            if constexpr (DO_AUP) {
+                T t = T(0);
+#pragma unroll
+                for (int i = 0; i < 24; ++i)
+                    if (PP.a[i][s] >= 0 && (i & 7) != 0) t = fma(R.A[PP.a[i][s]], xu[i >> 3][i & 7], t);
+                acc = a.cAup * t;
+            }
+            if constexpr (DO_S) acc = fma(kS * R.M[s], xp[s], acc);
+            if constexpr (DO_C) {
+                T t = T(0);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (PP.l[s][j] >= 0) t = fma(R.L[PP.l[s][j]], xp[j], t);
+                acc = fma(kC, t, acc);
+            }
+            return acc;
+        };
+        if constexpr (OUT_U) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const T hi0 = out_u(c, 4);
+                ob[c][0] += hi0;
+                ot[c][0] = -hi0;
+#pragma unroll
+                for (int q = 1; q < 4; ++q) {
+                    const T lo = out_u(c, q), hi = out_u(c, q | 4);
+                    ob[c][q] += lo + hi;
+                    ot[c][q] = lo - hi;
                 }
             }
-            if constexpr (IN_P) {
+        }
+        if constexpr (OUT_P) {
 #pragma unroll
-                for (int j = 0; j < BP; ++j) {
-                    const int s = ST.ps[b][j];
-                    xp[j] = (s & 4) ? (tb[IPI][s & 3] - tt[IPI][s & 3]) : (tb[IPI][s & 3] + tt[IPI][s & 3]);
-                }
-            }
-            if constexpr (OUT_U) {
-#pragma unroll
-                for (int k = 0; k < BU; ++k) {
-                    T acc = T(0);
-                    if constexpr (DO_K) {
-                        T t = T(0);
-#pragma unroll
-                        for (int k2 = 0; k2 < BU; ++k2) t = fma(R.K[(b * BU + k) * BU + k2], xu[k2], t);
-                        acc = kE * t;
-                    }
-                    if constexpr (DO_APU) {
-                        T t = T(0);
-#pragma unroll
-                        for (int j = 0; j < BP; ++j) t = fma(R.A[(b * BU + k) * BP + j], xp[j], t);
-                        acc = fma(a.cApu, t, acc);
-                    }
-                    const int c = ST.uc[b][k], s = ST.us[b][k];
-                    ob[c][s & 3] += acc;
-                    if (s & 4) ot[c][s & 3] -= acc; else ot[c][s & 3] += acc;
-                }
-            }
-            if constexpr (OUT_P) {
-#pragma unroll
-                for (int j = 0; j < BP; ++j) {
-                    T acc = T(0);
-                    if constexpr (DO_AUP) {
-                        T t = T(0);
-#pragma unroll
-                        for (int k = 0; k < BU; ++k) t = fma(R.A[(b * BU + k) * BP + j], xu[k], t);
-                        acc = a.cAup * t;
-                    }
-                    if constexpr (DO_S) {
-                        T t = T(0);
-#pragma unroll
-                        for (int j2 = 0; j2 < BP; ++j2) t = fma(R.M[(b * BP + j) * BP + j2], xp[j2], t);
-                        acc = fma(kS, t, acc);
-                    }
-                    if constexpr (DO_C) {
-                        T t = T(0);
-#pragma unroll
-                        for (int j2 = 0; j2 < BP; ++j2) t = fma(R.L[(b * BP + j) * BP + j2], xp[j2], t);
-                        acc = fma(kC, t, acc);
-                    }
-                    const int s = ST.ps[b][j];
-                    ob[OPI][s & 3] += acc;
-                    if (s & 4) ot[OPI][s & 3] -= acc; else ot[OPI][s & 3] += acc;
-                }
+            for (int q = 0; q < 4; ++q) {
+                const T lo = out_p(q), hi = out_p(q | 4);
+                ob[OPI][q] += lo + hi;
+                ot[OPI][q] = lo - hi;
             }
         }
     };
@@ -259,7 +263,7 @@ gm_bulk_apply_kernel(const BulkArgs<T> a, const __grid_constant__ RefOps<T> R)
         __syncthreads();
         fwd_xy(0, tt);
         if (fval) {
-            T ob[NO][4];
+            T ob[NO][4] = {};
             element(tb, tt, z0 - 1, ob, carry);
         }
 #pragma unroll

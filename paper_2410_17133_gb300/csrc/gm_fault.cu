@@ -204,21 +204,7 @@ int gm_launch_return_map(gm_ctx* c, const double* un, const double* du, cudaStre
 //   shat^2 = sum diag(K_b) u^2 + sum diag(A22) p^2      (free dofs)
 // ---------------------------------------------------------------------------
 struct ResArgs {
-    GridDesc g;
-    double dt;
-    const double* fu;
-    const double* fp;
-    const double* y1u;
-    const double* y1p;
-    const double* y2p;
-    const double* ut;
-    const double* pt;
-    const double* T;       // 3P
-    const double* dK;      // 3N
-    const double* dA;      // N
-    const uint8_t* mask;
-    double Aq;
-    double* b;             // 4N
+    ResidualInputs in;
     double* part;
     unsigned* counter;
     double* out;           // rhat^2, shat^2
@@ -226,60 +212,24 @@ struct ResArgs {
 
 __global__ void __launch_bounds__(256) gm_residual_kernel(const ResArgs a)
 {
-    const long long N = a.g.N;
+    const long long N = a.in.g.N;
     double v[2] = {0.0, 0.0};
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x) {
-        const unsigned m = a.mask[n];
-        const long long kk = n / a.g.nb;
-        const long long pid = n - kk * a.g.nb;
-        double lipsign = 0.0;
-        if (a.g.kf >= 0) {
-            if (kk == a.g.kf) lipsign = -1.0;
-            else if (kk == a.g.kf + 1) lipsign = 1.0;
-        }
-        double Ai = 0.0;
-        if (lipsign != 0.0) {
-            const int pi = (int)(pid % (a.g.nx + 1)), pj = (int)(pid / (a.g.nx + 1));
-            const int nqi = (pi > 0) + (pi < a.g.nx), nqj = (pj > 0) + (pj < a.g.ny);
-            Ai = a.Aq * 0.25 * nqi * nqj;
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            double r = 0.0;
-            if (!((m >> c) & 1u)) {
-                r = a.fu[c * N + n] - a.y1u[c * N + n];
-                if (lipsign != 0.0) r -= lipsign * Ai * a.T[c * a.g.nb + pid];
-                const double d = a.dK[c * N + n];
-                v[0] += r * r / d;
-                const double u = a.ut[c * N + n];
-                v[1] += d * u * u;
-            }
-            a.b[c * N + n] = r;
-        }
-        const bool slave = a.g.tied && kk == a.g.kf + 1;
-        double r = 0.0;
-        if (!slave && !((m >> 3) & 1u)) {
-            r = a.dt * a.fp[n] - a.y1p[n] - a.y2p[n];
-            const double d = a.dA[n];
-            v[0] += r * r / d;
-            const double p = a.pt[n];
-            v[1] += d * p * p;
-        }
-        a.b[3 * N + n] = r;
-    }
+         n += (long long)gridDim.x * blockDim.x)
+        gm_residual_node(a.in, n, v);
     if (gm_grid_sum<2>(v, a.part, a.counter)) {
         a.out[0] = v[0];
         a.out[1] = v[1];
     }
 }
 
-int gm_launch_residual(gm_ctx* c, const double* y1u, const double* y1p, const double* y2p,
-                       const double* ut, const double* pt, double* b, cudaStream_t s, double* out2)
+ResidualInputs gm_residual_inputs(const gm_ctx* c, const double* y1u, const double* y1p, const double* y2p,
+                                  const double* ut, const double* pt, double* b)
 {
-    ResArgs a;
+    ResidualInputs a;
     a.g = c->g;
     a.dt = c->dt;
+    a.Aq = c->Aq;
     a.fu = c->dfu.as<double>();
     a.fp = c->dfp.as<double>();
     a.y1u = y1u; a.y1p = y1p; a.y2p = y2p; a.ut = ut; a.pt = pt;
@@ -287,8 +237,15 @@ int gm_launch_residual(gm_ctx* c, const double* y1u, const double* y1p, const do
     a.dK = c->ddiagK.as<double>();
     a.dA = c->ddiagA.as<double>();
     a.mask = c->dmask.as<uint8_t>();
-    a.Aq = c->Aq;
     a.b = b;
+    return a;
+}
+
+int gm_launch_residual(gm_ctx* c, const double* y1u, const double* y1p, const double* y2p,
+                       const double* ut, const double* pt, double* b, cudaStream_t s, double* out2)
+{
+    ResArgs a;
+    a.in = gm_residual_inputs(c, y1u, y1p, y2p, ut, pt, b);
     a.part = c->dpart.as<double>();
     a.counter = c->dcount.as<unsigned>();
     a.out = out2;

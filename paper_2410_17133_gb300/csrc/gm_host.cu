@@ -123,13 +123,14 @@ bool ref_cell(const double h[3], const double sh[2], double nu, double K[24][24]
 
 inline double hsgn(int s, int a) { return (gm_popc3(s & a) & 1) ? -1.0 : 1.0; }
 
-// Parity transform + sector packing; returns false if an entry outside the
-// sector blocks is not negligible (wrong symmetry class).
+// Parity transform and packing of the entries the class's pattern allows;
+// returns false if an entry outside the pattern is not negligible (the cell
+// does not belong to the class, or the pattern rule does not hold).
 template <int CLS>
 bool pack_ref(const double K[24][24], const double A[24][8], const double M[8][8],
               const double L[8][8], RefOps<double>& R)
 {
-    constexpr SecTab ST = gm_make_sectab(CLS);
+    constexpr ParPat PP = gm_make_parpat(CLS);
     static double Kt[24][24], At[24][8], Mt[8][8], Lt[8][8];   // index (c*8+s)
     for (int c = 0; c < 3; ++c)
         for (int s = 0; s < 8; ++s) {
@@ -158,7 +159,6 @@ bool pack_ref(const double K[24][24], const double A[24][8], const double M[8][8
             Mt[s][s2] = vm / 64.0;
             Lt[s][s2] = vl / 64.0;
         }
-    // off-block check
     double kmax = 0, amax = 0, mmax = 0, lmax = 0;
     for (int i = 0; i < 24; ++i) {
         for (int j = 0; j < 24; ++j) kmax = std::max(kmax, std::fabs(Kt[i][j]));
@@ -170,43 +170,34 @@ bool pack_ref(const double K[24][24], const double A[24][8], const double M[8][8
             lmax = std::max(lmax, std::fabs(Lt[i][j]));
         }
     const double tol = 1e-12;
-    for (int c = 0; c < 3; ++c)
-        for (int s = 0; s < 8; ++s) {
-            const int b = gm_ulabel(CLS, c, s);
-            for (int c2 = 0; c2 < 3; ++c2)
-                for (int s2 = 0; s2 < 8; ++s2)
-                    if (gm_ulabel(CLS, c2, s2) != b && std::fabs(Kt[c * 8 + s][c2 * 8 + s2]) > tol * kmax) return false;
-            for (int s2 = 0; s2 < 8; ++s2)
-                if (gm_plabel(CLS, s2) != b && std::fabs(At[c * 8 + s][s2]) > tol * amax) return false;
-        }
-    for (int s = 0; s < 8; ++s)
-        for (int s2 = 0; s2 < 8; ++s2)
-            if (gm_plabel(CLS, s) != gm_plabel(CLS, s2) &&
-                (std::fabs(Mt[s][s2]) > tol * mmax || std::fabs(Lt[s][s2]) > tol * lmax))
-                return false;
     std::memset(&R, 0, sizeof(R));
-    for (int b = 0; b < ST.nb; ++b) {
-        for (int k = 0; k < ST.bu; ++k) {
-            const int ik = ST.uc[b][k] * 8 + ST.us[b][k];
-            for (int k2 = 0; k2 < ST.bu; ++k2)
-                R.K[(b * ST.bu + k) * ST.bu + k2] = Kt[ik][ST.uc[b][k2] * 8 + ST.us[b][k2]];
-            for (int j = 0; j < ST.bp; ++j) R.A[(b * ST.bu + k) * ST.bp + j] = At[ik][ST.ps[b][j]];
+    for (int i = 0; i < 24; ++i) {
+        for (int j = 0; j < 24; ++j) {
+            if (PP.k[i][j] >= 0) R.K[PP.k[i][j]] = Kt[i][j];
+            else if (std::fabs(Kt[i][j]) > tol * kmax) return false;
         }
-        for (int j = 0; j < ST.bp; ++j)
-            for (int j2 = 0; j2 < ST.bp; ++j2) {
-                R.M[(b * ST.bp + j) * ST.bp + j2] = Mt[ST.ps[b][j]][ST.ps[b][j2]];
-                R.L[(b * ST.bp + j) * ST.bp + j2] = Lt[ST.ps[b][j]][ST.ps[b][j2]];
-            }
+        for (int j = 0; j < 8; ++j) {
+            if (PP.a[i][j] >= 0) R.A[PP.a[i][j]] = At[i][j];
+            else if (std::fabs(At[i][j]) > tol * amax) return false;
+        }
     }
+    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) {
+            if (i == j) R.M[i] = Mt[i][i];
+            else if (std::fabs(Mt[i][j]) > tol * mmax) return false;
+            if (PP.l[i][j] >= 0) R.L[PP.l[i][j]] = Lt[i][j];
+            else if (std::fabs(Lt[i][j]) > tol * lmax) return false;
+        }
     return true;
 }
 
 template <typename D, typename S>
 void cast_ref(const RefOps<S>& a, RefOps<D>& b)
 {
-    for (int i = 0; i < 288; ++i) b.K[i] = (D)a.K[i];
-    for (int i = 0; i < 96; ++i) b.A[i] = (D)a.A[i];
-    for (int i = 0; i < 32; ++i) { b.M[i] = (D)a.M[i]; b.L[i] = (D)a.L[i]; }
+    for (int i = 0; i < GM_PP_MAXK; ++i) b.K[i] = (D)a.K[i];
+    for (int i = 0; i < GM_PP_MAXA; ++i) b.A[i] = (D)a.A[i];
+    for (int i = 0; i < 8; ++i) b.M[i] = (D)a.M[i];
+    for (int i = 0; i < GM_PP_MAXL; ++i) b.L[i] = (D)a.L[i];
 }
 
 int bind_impl(gm_ctx* c);
@@ -809,6 +800,7 @@ int bind_impl(gm_ctx* c)
     c->g.N = N;
     c->g.nb = (long long)(c->nx + 1) * (c->ny + 1);
     c->P = c->has_fault ? c->g.nb : 0;
+    if (3 * N >= (1LL << 31)) return c->set_err(GM_EINVAL, "bind: more than 715,827,882 nodes (32-bit vector offsets)");
     if (c->fixed.empty()) c->fixed.assign(4 * N, 0);
     if (c->fu.empty()) c->fu.assign(3 * N, 0.0);
     if (c->fpv.empty()) c->fpv.assign(N, 0.0);
@@ -823,8 +815,11 @@ int bind_impl(gm_ctx* c)
     bool ok = c->cls == GM_CLS_BOX ? pack_ref<GM_CLS_BOX>(K, A, M, L, c->R64)
             : c->cls == GM_CLS_MONO ? pack_ref<GM_CLS_MONO>(K, A, M, L, c->R64)
                                     : pack_ref<GM_CLS_GEN>(K, A, M, L, c->R64);
-    if (!ok) return c->set_err(GM_EINVAL, "bind: cell operators break the expected symmetry");
+    if (!ok) return c->set_err(GM_EINVAL, "bind: cell operators break the expected parity pattern");
     cast_ref(c->R64, c->R32);
+    for (int i = 0; i < GM_PP_MAXK; ++i) c->R32p.K[i] = make_float2(c->R32.K[i], c->R32.K[i]);
+    for (int i = 0; i < 8; ++i) c->R32p.M[i] = make_float2(c->R32.M[i], c->R32.M[i]);
+    for (int i = 0; i < GM_PP_MAXL; ++i) c->R32p.L[i] = make_float2(c->R32.L[i], c->R32.L[i]);
     for (int a = 0; a < 8; ++a)
         for (int b = 0; b < 8; ++b) c->Lref[8 * a + b] = L[a][b];
     c->has_fpair = false;
@@ -890,18 +885,17 @@ int bind_impl(gm_ctx* c)
     if (const char* pp = std::getenv("GM_PAIR_PREC")) c->pair_prec = std::atoi(pp) != 0;
     // reduction partials: the fixed-grid reductions use 2 * GM_RED_BLOCKS slots,
     // a fused PCG step one per bulk CTA plus one per fault block
+    // (bulk kernels: at most one CTA per 15 x 15 tile and pair of node planes)
     const int gxp = (c->nx + 1 + 14) / 15, gyp = (c->ny + 1 + 14) / 15;
     const long long xyp = (long long)gxp * gyp;
-    const long long nzc = std::max(1LL, (4LL * c->sm_count + xyp - 1) / xyp);
-    const long long zcp = c->zchunk_override > 0 ? (long long)c->zchunk_override
-                                                 : std::max(4LL, (c->g.nplanes + nzc - 1) / nzc);
+    const long long zcp = c->zchunk_override > 0 ? std::min<long long>(2, c->zchunk_override) : 2LL;
     c->bulk_grid = (int)(xyp * ((c->g.nplanes + zcp - 1) / zcp));
     const size_t part_bytes = (size_t)8 * std::max<long long>(4LL * GM_RED_BLOCKS,
                                                               c->bulk_grid + (c->g.nb + 255) / 256 + 64);
     struct A_ { DevBuf* b; size_t bytes; } allocs[] = {
         {&c->dE64, (size_t)nel * 8}, {&c->dK64, (size_t)nel * 8},
         {&c->dE32, (size_t)nel * 4}, {&c->dK32, (size_t)nel * 4},
-        {&c->dmask, (size_t)N}, {&c->dfu, (size_t)N3 * 8}, {&c->dfp, (size_t)N * 8},
+        {&c->dmask, (size_t)N + 64}, {&c->dfu, (size_t)N3 * 8}, {&c->dfp, (size_t)N * 8},
         {&c->du_n, (size_t)N3 * 8}, {&c->dp_n, (size_t)N * 8},
         {&c->ddlie_n, (size_t)2 * P * 8}, {&c->dflags_n, (size_t)P},
         {&c->dstate, (size_t)P}, {&c->dprevstate, (size_t)P}, {&c->dtn, (size_t)P * 8},
@@ -965,8 +959,11 @@ int bind_impl(gm_ctx* c)
         for (int f = 0; f < 4; ++f)
             if (c->fixed[f * N + n]) mask[n] |= (uint8_t)(1u << f);
     GM_CUDA_TRY(c, cudaMemcpy(c->dmask.p, mask.data(), N, cudaMemcpyHostToDevice));
+    GM_CUDA_TRY(c, cudaMemset(static_cast<uint8_t*>(c->dmask.p) + N, 0, 64));
     c->bound = true;   // loads upload below needs the grid
-    int rc = upload_loads(c);
+    int rc = gm_prepare_bulk32(c);
+    if (rc) { c->bound = false; return rc; }
+    rc = upload_loads(c);
     if (rc) { c->bound = false; return rc; }
     GM_CUDA_TRY(c, cudaMemset(c->du_n.p, 0, N3 * 8));
     GM_CUDA_TRY(c, cudaMemset(c->dp_n.p, 0, N * 8));

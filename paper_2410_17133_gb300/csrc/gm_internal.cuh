@@ -32,66 +32,132 @@ enum : int {
     GM_MODE_RES2 = GM_M_AUP | GM_M_S                            // A_up du + S dp
 };
 
-// Symmetry classes of the affine cell (number of parity sectors).
+// ---------------------------------------------------------------------------
+// Reference-cell operators in the parity (Walsh-Hadamard) basis
+//
+// The 8 nodal values of a field on a cell are replaced by their parity modes
+// x_s = sum_a (-1)^popc(s & a) v_a (node a = ax + 2 ay + 4 az, s = sx + 2 sy +
+// 4 sz).  In the trilinear space the modes are the monomials 1, xi_x, xi_y,
+// xi_x xi_y, ... and the derivative along reference axis d maps mode s (with
+// bit d set) to mode s ^ e_d; 2x2x2 Gauss quadrature keeps distinct modes
+// orthogonal.  An entry between modes s and s2 of the element operators can
+// therefore be nonzero only if there are reference directions d (a bit of s)
+// and d2 (a bit of s2) with s ^ e_d == s2 ^ e_d2, and if the physical
+// coefficient that couples (field c, derivative d) with (field c2, derivative
+// d2) can be nonzero.  For the affine cell
+//   X = (h0 xi0, h1 xi1, h2 xi2 + s0 h0 xi0 + s1 h1 xi1)
+// reference derivative d feeds physical derivative i when d == i or when
+// d = z and the shear s0 (i = x) or s1 (i = y) is nonzero.  The tables below
+// list every entry this rule allows; the host checks at bind that all other
+// entries of the actual operators vanish (else the bind fails), and the
+// kernels multiply only the allowed entries.  K (elasticity) has 45 / 73 / 109
+// allowed entries for a box / a cell sheared in x-z / a general cell, against
+// 576 dense; A (Biot) 12 / 16 / 20; M (storage) is diagonal; L (Darcy)
+// 7 / 11 / 15.
+// ---------------------------------------------------------------------------
+
+// Symmetry classes of the affine cell.
 enum : int { GM_CLS_BOX = 0, GM_CLS_MONO = 1, GM_CLS_GEN = 2 };
-
-// ---------------------------------------------------------------------------
-// Reference-cell operators in the parity (Walsh-Hadamard) basis, packed by
-// sector.  For class nb sectors, bu = 24/nb displacement entries and
-// bp = 8/nb pressure entries per sector.
-//   K[b][k][k'] (bu x bu)  for E = 1
-//   A[b][k][j]  (bu x bp)  for alpha = 1
-//   M[b][j][j'], L[b][j][j'] (bp x bp) for 1/M = 1 and k/mu = 1
-// All already carry the 1/64 of the inverse transform.
-// ---------------------------------------------------------------------------
-template <typename T>
-struct RefOps {
-    T K[288];
-    T A[96];
-    T M[32];
-    T L[32];
-};
-
-// Sector membership, computed at compile time from the class.
-struct SecTab {
-    int nb, bu, bp;
-    int uc[8][12];
-    int us[8][12];
-    int ps[8][4];
-};
 
 __host__ __device__ constexpr int gm_popc3(int s) { return (s & 1) + ((s >> 1) & 1) + ((s >> 2) & 1); }
 
-// Character labels of the reflection group of the cell.  u_c at parity index s
-// transforms like s XOR e_c under the three mirror planes of a box; a cell
-// sheared in x-z keeps the y mirror and the central inversion; a general
-// parallelepiped keeps only the inversion.
-__host__ __device__ constexpr int gm_ulabel(int cls, int c, int s) {
-    return cls == GM_CLS_BOX ? (s ^ (1 << c))
-         : cls == GM_CLS_MONO ? ((((s >> 1) & 1) ^ (c == 1 ? 1 : 0)) + 2 * (1 ^ (gm_popc3(s) & 1)))
-                              : (1 ^ (gm_popc3(s) & 1));
+// reference derivative d contributes to physical derivative i
+__host__ __device__ constexpr bool gm_jac_feeds(int cls, int d, int i)
+{
+    return d == i || (d == 2 && ((i == 0 && cls != GM_CLS_BOX) || (i == 1 && cls == GM_CLS_GEN)));
 }
-__host__ __device__ constexpr int gm_plabel(int cls, int s) {
-    return cls == GM_CLS_BOX ? s
-         : cls == GM_CLS_MONO ? (((s >> 1) & 1) + 2 * (gm_popc3(s) & 1))
-                              : (gm_popc3(s) & 1);
+
+// isotropic elasticity couples (field c, reference derivative d) with
+// (field c2, reference derivative d2): lambda div u div v + mu (grad u + grad u^T) : grad v
+__host__ __device__ constexpr bool gm_elastic_couples(int cls, int c, int d, int c2, int d2)
+{
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k)
+            if (gm_jac_feeds(cls, d, i) && gm_jac_feeds(cls, d2, k) &&
+                ((c == i && c2 == k) || (c == c2 && i == k) || (c == k && c2 == i)))
+                return true;
+    return false;
 }
-__host__ __device__ constexpr SecTab gm_make_sectab(int cls) {
-    SecTab t{};
-    t.nb = cls == GM_CLS_BOX ? 8 : (cls == GM_CLS_MONO ? 4 : 2);
-    t.bu = 24 / t.nb;
-    t.bp = 8 / t.nb;
-    for (int b = 0; b < t.nb; ++b) {
-        int k = 0;
-        for (int c = 0; c < 3; ++c)
-            for (int s = 0; s < 8; ++s)
-                if (gm_ulabel(cls, c, s) == b) { t.uc[b][k] = c; t.us[b][k] = s; ++k; }
-        int j = 0;
-        for (int s = 0; s < 8; ++s)
-            if (gm_plabel(cls, s) == b) { t.ps[b][j] = s; ++j; }
+
+__host__ __device__ constexpr bool gm_shares_mode(int s, int d, int s2, int d2)
+{
+    return ((s >> d) & 1) && ((s2 >> d2) & 1) && ((s ^ (1 << d)) == (s2 ^ (1 << d2)));
+}
+
+__host__ __device__ constexpr bool gm_kpat(int cls, int c, int s, int c2, int s2)
+{
+    for (int d = 0; d < 3; ++d)
+        for (int d2 = 0; d2 < 3; ++d2)
+            if (gm_shares_mode(s, d, s2, d2) && gm_elastic_couples(cls, c, d, c2, d2)) return true;
+    return false;
+}
+
+// A_pu: divergence of u (physical derivative c of field c) against pressure mode s2
+__host__ __device__ constexpr bool gm_apat(int cls, int c, int s, int s2)
+{
+    for (int d = 0; d < 3; ++d)
+        if (((s >> d) & 1) && (s ^ (1 << d)) == s2 && gm_jac_feeds(cls, d, c)) return true;
+    return false;
+}
+
+__host__ __device__ constexpr bool gm_lpat(int cls, int s, int s2)
+{
+    for (int d = 0; d < 3; ++d)
+        for (int d2 = 0; d2 < 3; ++d2)
+            if (gm_shares_mode(s, d, s2, d2))
+                for (int i = 0; i < 3; ++i)
+                    if (gm_jac_feeds(cls, d, i) && gm_jac_feeds(cls, d2, i)) return true;
+    return false;
+}
+
+// Packed positions of the allowed entries (row-major), -1 elsewhere.  Rows and
+// columns are indexed c * 8 + s for displacement modes and s for pressure modes.
+struct ParPat {
+    int nk, na, nl;
+    signed char k[24][24];
+    signed char a[24][8];
+    signed char l[8][8];
+};
+
+__host__ __device__ constexpr ParPat gm_make_parpat(int cls)
+{
+    ParPat t{};
+    t.nk = t.na = t.nl = 0;
+    for (int i = 0; i < 24; ++i) {
+        for (int j = 0; j < 24; ++j)
+            t.k[i][j] = gm_kpat(cls, i / 8, i % 8, j / 8, j % 8) ? (signed char)(t.nk++) : (signed char)-1;
+        for (int j = 0; j < 8; ++j)
+            t.a[i][j] = gm_apat(cls, i / 8, i % 8, j) ? (signed char)(t.na++) : (signed char)-1;
     }
+    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) t.l[i][j] = gm_lpat(cls, i, j) ? (signed char)(t.nl++) : (signed char)-1;
     return t;
 }
+
+constexpr int GM_PP_MAXK = 112, GM_PP_MAXA = 24, GM_PP_MAXL = 16;
+static_assert(gm_make_parpat(GM_CLS_BOX).nk == 45 && gm_make_parpat(GM_CLS_MONO).nk == 73 &&
+              gm_make_parpat(GM_CLS_GEN).nk == 109, "elasticity pattern sizes");
+static_assert(gm_make_parpat(GM_CLS_GEN).nk <= GM_PP_MAXK && gm_make_parpat(GM_CLS_GEN).na <= GM_PP_MAXA &&
+              gm_make_parpat(GM_CLS_GEN).nl <= GM_PP_MAXL, "packed operator sizes");
+
+// Allowed entries of the reference operators (E = 1, alpha = 1, 1/M = 1,
+// k/mu = 1), packed in the order of gm_make_parpat(cls); the 1/64 of the
+// inverse transform is folded in.  M holds the diagonal.
+template <typename T>
+struct RefOps {
+    T K[GM_PP_MAXK];
+    T A[GM_PP_MAXA];
+    T M[8];
+    T L[GM_PP_MAXL];
+};
+
+// The FP32 pattern entries, each duplicated as a pair (lo, hi) so that one
+// packed instruction of the FP32 bulk kernel applies it to two elements.
+struct RefPairs32 {
+    float2 K[GM_PP_MAXK];
+    float2 M[8];
+    float2 L[GM_PP_MAXL];
+};
 
 // Per-node mask bits: 1,2,4 = ux,uy,uz fixed, 8 = p fixed.
 // Tied upper-lip pressures are slaves (handled by index, not by this mask).
@@ -193,6 +259,70 @@ struct LawArgs {
 };
 
 
+// Inputs of the Newton residual (RHS of Eq. linear_system, Sec. 3.3.1) shared by
+// gm_residual and gm_residual_noalloc.
+struct ResidualInputs {
+    GridDesc g;
+    double dt, Aq;
+    const double* fu;     // 3N loads
+    const double* fp;     // N sources
+    const double* y1u;    // 3N: K_b u - A_pu p
+    const double* y1p;    // N: dt C p
+    const double* y2p;    // N: A_up du + S dp
+    const double* ut;     // 3N total displacement
+    const double* pt;     // N total pressure
+    const double* T;      // 3P incremental cohesive traction
+    const double* dK;     // 3N diag(K_b)
+    const double* dA;     // N diag(A22)
+    const uint8_t* mask;
+    double* b;            // 4N output
+};
+
+// Residual of node n written to b (0 on constrained and tied-slave dofs);
+// v[0] += its terms of sum b1^2/diag(K_b) + sum b2^2/diag(A22), v[1] += its
+// terms of sum diag(K_b) u^2 + sum diag(A22) p^2.
+__device__ __forceinline__ void gm_residual_node(const ResidualInputs& a, long long n, double (&v)[2])
+{
+    const long long N = a.g.N;
+    const unsigned m = a.mask[n];
+    const long long kk = n / a.g.nb;
+    const long long pid = n - kk * a.g.nb;
+    double lipsign = 0.0;
+    if (a.g.kf >= 0) {
+        if (kk == a.g.kf) lipsign = -1.0;
+        else if (kk == a.g.kf + 1) lipsign = 1.0;
+    }
+    double Ai = 0.0;
+    if (lipsign != 0.0) {
+        const int pi = (int)(pid % (a.g.nx + 1)), pj = (int)(pid / (a.g.nx + 1));
+        const int nqi = (pi > 0) + (pi < a.g.nx), nqj = (pj > 0) + (pj < a.g.ny);
+        Ai = a.Aq * 0.25 * nqi * nqj;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double r = 0.0;
+        if (!((m >> c) & 1u)) {
+            r = a.fu[c * N + n] - a.y1u[c * N + n];
+            if (lipsign != 0.0) r -= lipsign * Ai * a.T[c * a.g.nb + pid];
+            const double d = a.dK[c * N + n];
+            v[0] += r * r / d;
+            const double u = a.ut[c * N + n];
+            v[1] += d * u * u;
+        }
+        a.b[c * N + n] = r;
+    }
+    const bool slave = a.g.tied && kk == a.g.kf + 1;
+    double r = 0.0;
+    if (!slave && !((m >> 3) & 1u)) {
+        r = a.dt * a.fp[n] - a.y1p[n] - a.y2p[n];
+        const double d = a.dA[n];
+        v[0] += r * r / d;
+        const double p = a.pt[n];
+        v[1] += d * p * p;
+    }
+    a.b[3 * N + n] = r;
+}
+
 // ---------------------------------------------------------------------------
 // Device buffer
 // ---------------------------------------------------------------------------
@@ -265,6 +395,7 @@ struct gm_ctx {
     int cls = GM_CLS_BOX;
     RefOps<double> R64{};
     RefOps<float> R32{};
+    RefPairs32 R32p{};
     double Kblk_ref[8][9] = {};   // nodal 3x3 diagonal blocks of K_ref (E = 1)
     double Mdiag_ref[8] = {}, Ldiag_ref[8] = {};
     double Aq = 0, nrm[3] = {0, 0, 1}, t1[3] = {1, 0, 0}, t2[3] = {0, 1, 0};
@@ -364,12 +495,15 @@ int gm_launch_apply_f32(gm_ctx* c, int mode, double cK, double cApu, double cAup
 // Fault law, residual, preconditioners
 int gm_launch_return_map(gm_ctx* c, const double* un, const double* du, cudaStream_t s);
 int gm_upload_permeability(gm_ctx* c);                 // kap arrays + diagonals from c->kperm
+ResidualInputs gm_residual_inputs(const gm_ctx* c, const double* y1u, const double* y1p, const double* y2p,
+                                  const double* ut, const double* pt, double* b);
 int gm_launch_residual(gm_ctx* c, const double* y1u, const double* y1p, const double* y2p,
                        const double* ut, const double* pt, double* b, cudaStream_t s,
                        double* out2 /* device: rhat^2, shat^2 */);
 int gm_launch_diag(gm_ctx* c, cudaStream_t s);            // dK (bulk), dA (needs dt)
 int gm_launch_block_jacobi(gm_ctx* c, cudaStream_t s);    // K_T 3x3 inverse blocks
 // multigrid preconditioner of the FP32 K_T solves (gm_mg.cu)
+int gm_prepare_bulk32(gm_ctx* c);                     // kernel attributes, at bind
 int gm_launch_bulk_k_f32(gm_ctx* c, const float* x, float* y, cudaStream_t s, const int* skip);
 int gm_launch_bulk_k_f64(gm_ctx* c, const double* x, double* y, cudaStream_t s, const int* skip);
 int gm_mg_prepare(gm_ctx* c, int prec, cudaStream_t s);   // GM_EINVAL: grid not coarsenable (caller falls back)

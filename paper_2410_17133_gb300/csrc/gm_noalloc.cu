@@ -11,7 +11,6 @@
 // or different contexts on the same device) race on it and must be serialised by
 // the caller.
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "gm_internal.cuh"
@@ -35,20 +34,7 @@ static __device__ __align__(256) double gm_noalloc_scratch[kScratchDoubles];
 namespace {
 
 struct NoAllocArgs {
-    GridDesc g;
-    double dt, Aq;
-    const double* fu;
-    const double* fp;
-    const double* y1u;
-    const double* y1p;
-    const double* y2p;
-    const double* ut;
-    const double* pt;
-    const double* T;
-    const double* dK;
-    const double* dA;
-    const uint8_t* mask;
-    double* b;
+    ResidualInputs in;
     double* scratch;   // device address of gm_noalloc_scratch
 };
 
@@ -75,47 +61,9 @@ __global__ void __launch_bounds__(kThreads) gm_residual_noalloc_kernel(const NoA
 {
     __shared__ double sh[64];
     __shared__ bool last;
-    const long long N = a.g.N;
     const long long n = (long long)blockIdx.x * kThreads + threadIdx.x;
     double v[2] = {0.0, 0.0};
-    if (n < N) {
-        const unsigned m = a.mask[n];
-        const long long kk = n / a.g.nb;
-        const long long pid = n - kk * a.g.nb;
-        double lipsign = 0.0;
-        if (a.g.kf >= 0) {
-            if (kk == a.g.kf) lipsign = -1.0;
-            else if (kk == a.g.kf + 1) lipsign = 1.0;
-        }
-        double Ai = 0.0;
-        if (lipsign != 0.0) {
-            const int pi = (int)(pid % (a.g.nx + 1)), pj = (int)(pid / (a.g.nx + 1));
-            const int nqi = (pi > 0) + (pi < a.g.nx), nqj = (pj > 0) + (pj < a.g.ny);
-            Ai = a.Aq * 0.25 * nqi * nqj;
-        }
-        for (int c = 0; c < 3; ++c) {
-            double r = 0.0;
-            if (!((m >> c) & 1u)) {
-                r = a.fu[c * N + n] - a.y1u[c * N + n];
-                if (lipsign != 0.0) r -= lipsign * Ai * a.T[c * a.g.nb + pid];
-                const double d = a.dK[c * N + n];
-                v[0] += r * r / d;
-                const double u = a.ut[c * N + n];
-                v[1] += d * u * u;
-            }
-            a.b[c * N + n] = r;
-        }
-        const bool slave = a.g.tied && kk == a.g.kf + 1;
-        double r = 0.0;
-        if (!slave && !((m >> 3) & 1u)) {
-            r = a.dt * a.fp[n] - a.y1p[n] - a.y2p[n];
-            const double d = a.dA[n];
-            v[0] += r * r / d;
-            const double p = a.pt[n];
-            v[1] += d * p * p;
-        }
-        a.b[3 * N + n] = r;
-    }
+    if (n < a.in.g.N) gm_residual_node(a.in, n, v);
     na_block_sum(v, sh);
     double* part = a.scratch;
     unsigned* counter = reinterpret_cast<unsigned*>(a.scratch + kCounterSlot);
@@ -143,27 +91,21 @@ __global__ void __launch_bounds__(kThreads) gm_residual_noalloc_kernel(const NoA
     }
 }
 
-std::mutex g_mutex;
-void* g_addr[256] = {};
-
-// Device address of the scratch array on the context's device, looked up once
-// per device with that device current.
+// Device address of the scratch array in the context's device, looked up on
+// every call with that device current (the lookup allocates nothing), so a
+// context re-created after cudaDeviceReset or a different current context never
+// sees a stale address.
 int scratch_address(gm_ctx* c, double** out)
 {
-    if (c->device < 0 || c->device >= 256) return c->set_err(GM_EINVAL, "residual_noalloc: device index out of range");
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (g_addr[c->device] == nullptr) {
-        int cur = -1;
-        GM_CUDA_TRY(c, cudaGetDevice(&cur));
-        if (cur != c->device) GM_CUDA_TRY(c, cudaSetDevice(c->device));
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, gm_noalloc_scratch);
-        if (cur != c->device) cudaSetDevice(cur);
-        if (e != cudaSuccess || p == nullptr)
-            return c->set_err(GM_ECUDA, std::string("residual_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_addr[c->device] = p;
-    }
-    *out = static_cast<double*>(g_addr[c->device]);
+    int cur = -1;
+    GM_CUDA_TRY(c, cudaGetDevice(&cur));
+    if (cur != c->device) GM_CUDA_TRY(c, cudaSetDevice(c->device));
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, gm_noalloc_scratch);
+    if (cur != c->device) cudaSetDevice(cur);
+    if (e != cudaSuccess || p == nullptr)
+        return c->set_err(GM_ECUDA, std::string("residual_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    *out = static_cast<double*>(p);
     return GM_OK;
 }
 
@@ -199,17 +141,7 @@ extern "C" int gm_residual_noalloc(gm_ctx* c, const double* du, const double* dp
     // the counter must start at zero whatever an earlier call left behind
     GM_CUDA_TRY(c, cudaMemsetAsync(scratch + kCounterSlot, 0, sizeof(double), s));
     NoAllocArgs a;
-    a.g = c->g;
-    a.dt = c->dt;
-    a.Aq = c->Aq;
-    a.fu = c->dfu.as<double>();
-    a.fp = c->dfp.as<double>();
-    a.y1u = y1u; a.y1p = y1p; a.y2p = y2p; a.ut = ut; a.pt = pt;
-    a.T = c->dT.as<double>();
-    a.dK = c->ddiagK.as<double>();
-    a.dA = c->ddiagA.as<double>();
-    a.mask = c->dmask.as<uint8_t>();
-    a.b = b;
+    a.in = gm_residual_inputs(c, y1u, y1p, y2p, ut, pt, b);
     a.scratch = scratch;
     const int nblk = (int)((N + kThreads - 1) / kThreads);
     gm_residual_noalloc_kernel<<<nblk, kThreads, 0, s>>>(a);

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -130,6 +131,12 @@ struct DBuf {
 
 }  // namespace
 
+// Largest node, tetrahedron or fault-triangle count: all device index arithmetic
+// (12 gradients per element, 9 frame entries per pair, 3N field offsets) is in
+// 32-bit int, which this bound keeps in range.
+constexpr long long kTetMaxEntities = 1LL << 27;
+static_assert(12 * kTetMaxEntities < 2147483647LL, "tet index arithmetic must fit in int");
+
 struct gm_tet {
     int device = 0;
     std::string err;
@@ -191,7 +198,7 @@ int gm_tet_mesh(gm_tet* t, const double* nodes, int64_t n_nodes, const int64_t* 
     if (!t) return GM_EINVAL;
     if (!nodes || !tets || n_nodes < 4 || n_tets < 1) return t->set_err(GM_EINVAL, "tet mesh: empty mesh");
     // the kernels index element and nodal-block arrays (12 M, 9 N entries) with 32-bit ints
-    if (n_nodes > (1LL << 27) || n_tets > (1LL << 27)) return t->set_err(GM_EINVAL, "tet mesh: too large");
+    if (n_nodes > kTetMaxEntities || n_tets > kTetMaxEntities) return t->set_err(GM_EINVAL, "tet mesh: too large");
     const long long N = n_nodes, M = n_tets;
     std::vector<double> G(12 * M), V(M);
     std::vector<int> tv(4 * M);
@@ -1205,7 +1212,7 @@ extern "C" int gm_tet_fault(gm_tet* t, const int64_t* pairs, int64_t n_pairs, co
 {
     if (!t) return GM_EINVAL;
     if (!t->has_mesh) return t->set_err(GM_ESTATE, "tet fault: no mesh");
-    if (!pairs || !tris || !t1_ref || !fp || n_pairs < 1 || n_tris < 1 || n_pairs > t->N || n_tris > (1LL << 27))
+    if (!pairs || !tris || !t1_ref || !fp || n_pairs < 1 || n_tris < 1 || n_pairs > t->N || n_tris > kTetMaxEntities)
         return t->set_err(GM_EINVAL, "tet fault: bad arguments");
     if (!(fp->kn >= 0) || !(fp->ks > 0) || !(fp->f >= 0) || !(fp->w0 > 0) || !(fp->wk_par >= 0) || !(fp->MF > 0))
         return t->set_err(GM_EINVAL, "tet fault: invalid fault parameters");
@@ -1254,11 +1261,27 @@ extern "C" int gm_tet_fault(gm_tet* t, const int64_t* pairs, int64_t n_pairs, co
                 Lt[9 * q + 3 * a + b] = at * (dN[a][0] * (i11 * dN[b][0] + i12 * dN[b][1]) +
                                               dN[a][1] * (i12 * dN[b][0] + i22 * dN[b][1]));
     }
+    // Orientation: the pair normal is built from the triangles' vertex order, so
+    // that order must agree across the fault (an edge shared by two triangles
+    // runs in opposite directions in them) ...
+    {
+        std::unordered_map<unsigned long long, int> dir;
+        dir.reserve((size_t)(3 * NT));
+        for (long long q = 0; q < NT; ++q)
+            for (int v = 0; v < 3; ++v) {
+                const unsigned long long a = (unsigned)tri[3 * q + v], b = (unsigned)tri[3 * q + (v + 1) % 3];
+                if (a == b) return t->set_err(GM_EINVAL, "tet fault: triangle repeats a pair");
+                if (++dir[a * (unsigned long long)P + b] > 1)
+                    return t->set_err(GM_EINVAL, "tet fault: adjacent triangles are ordered inconsistently "
+                                                 "(an edge runs the same way in both)");
+            }
+    }
     std::vector<double> fr(9 * P);
     for (long long i = 0; i < P; ++i) {
         if (!(area[i] > 0.0)) return t->set_err(GM_EINVAL, "tet fault: a pair lies on no triangle");
         const double* ns = &nsum[3 * i];
         const double nl = std::sqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
+        if (!(nl > 1e-12 * area[i])) return t->set_err(GM_EINVAL, "tet fault: the triangle normals around a pair cancel");
         const double n[3] = {ns[0] / nl, ns[1] / nl, ns[2] / nl};
         const double dr = n[0] * t1_ref[0] + n[1] * t1_ref[1] + n[2] * t1_ref[2];
         double e[3] = {t1_ref[0] - dr * n[0], t1_ref[1] - dr * n[1], t1_ref[2] - dr * n[2]};
@@ -1271,6 +1294,30 @@ extern "C" int gm_tet_fault(gm_tet* t, const int64_t* pairs, int64_t n_pairs, co
             fr[c * P + i] = n[c];
             fr[(3 + c) * P + i] = t1[c];
             fr[(6 + c) * P + i] = t2[c];
+        }
+    }
+    // ... and the normal must point from the minus lip to the plus lip: every
+    // tetrahedron touching a minus-lip node lies on the -n side of it, every one
+    // touching a plus-lip node on the +n side, and none holds both lips of a pair.
+    for (long long e = 0; e < t->M; ++e) {
+        const int* tv = &t->htv[4 * e];
+        double cen[3] = {0.0, 0.0, 0.0};
+        for (int v = 0; v < 4; ++v)
+            for (int d = 0; d < 3; ++d) cen[d] += 0.25 * t->hX[3 * tv[v] + d];
+        for (int v = 0; v < 4; ++v) {
+            const int q = n2p[tv[v]];
+            if (q < 0) continue;
+            const bool minus = pm[q] == tv[v];
+            for (int w = 0; w < 4; ++w)
+                if (w != v && tv[w] == (minus ? pp[q] : pm[q]))
+                    return t->set_err(GM_EINVAL, "tet fault: a tetrahedron holds both lips of a pair");
+            double side = 0.0;
+            for (int d = 0; d < 3; ++d) side += (cen[d] - t->hX[3 * tv[v] + d]) * fr[d * P + q];
+            if (minus ? !(side < 0.0) : !(side > 0.0))
+                return t->set_err(GM_EINVAL, minus ? "tet fault: a minus-lip tetrahedron lies on the +n side "
+                                                     "(triangle order gives a normal from plus to minus)"
+                                                   : "tet fault: a plus-lip tetrahedron lies on the -n side "
+                                                     "(triangle order gives a normal from plus to minus)");
         }
     }
     for (long long i = 0; i < P; ++i) cnt[i + 1] += cnt[i];

@@ -35,7 +35,8 @@ def test_printed_marginally_pressurised_case_has_T_4():
 
 def test_printed_critically_stressed_tau0_is_rounded():
     """With the printed tau0 = 47.999 MPa the parameter evaluates to ~0.024, not
-    the stated 0.01: the printed shear load is rounded (reading in DESIGN)."""
+    the stated 0.01: the printed shear load is rounded, so the slip-front
+    workload sets tau0 from the stated ratio and T instead."""
     g = load("table1_slip_benchmark.json")
     T = analytic.stress_injection_parameter(g["tau0_CS"], g["f"], g["sigma0"], g["Q"], g["mu_f"], g["wk_par"])
     assert 0.02 < T < 0.03

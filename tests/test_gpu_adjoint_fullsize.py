@@ -7,7 +7,8 @@ random log-permeability directions (numpy default_rng(45)) and along the
 friction and log-source parameters.  Each finite-difference run must keep the
 contact/friction state history of the base run, else the difference quotient
 crosses a kink and the check is void.  GM_ADJOINT_FD_DIRECTIONS sets the
-number of permeability directions (default 2).  The half-size faulted aquifer
+number of permeability directions (default 16, the count the gradient
+workload asks for).  The half-size faulted aquifer
 carries a caprock-pressure gradient checked the same way along log Q."""
 import math
 import os
@@ -85,7 +86,7 @@ def test_log_permeability_directions(base):
     prob = base["prob"]
     k0 = np.asarray(prob.k, float)
     rng = np.random.default_rng(45)
-    nd = int(os.environ.get("GM_ADJOINT_FD_DIRECTIONS", "2"))
+    nd = int(os.environ.get("GM_ADJOINT_FD_DIRECTIONS", "16"))
     worst = 0.0
     for d in range(nd):
         v = rng.normal(size=k0.size)

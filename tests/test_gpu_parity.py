@@ -127,6 +127,37 @@ def test_apply_fp32(name, op):
         assert rel(y[:3].reshape(-1), yu_o) < 2e-5
 
 
+@pytest.mark.parametrize("zchunk", [0, 2, 3, 5])
+@pytest.mark.parametrize("name", list(CASES))
+def test_apply_fp32_kernel_all_cells_and_chunks(name, zchunk, monkeypatch):
+    """The FP32 bulk kernel (K_b, K_T and S + dt C applies) on every cell class,
+    tied and double-node lips and the fault-free grid, with the plane-chunk
+    length forced (GM_BULK_ZCHUNK) so that chunks start at, below and above
+    either lip: against the oracle evaluated on the same FP32 inputs, within
+    FP32 rounding (5e-6 relative L2)."""
+    dt = 1.7
+    if zchunk:
+        monkeypatch.setenv("GM_BULK_ZCHUNK", str(zchunk))
+    else:
+        monkeypatch.delenv("GM_BULK_ZCHUNK", raising=False)
+    prob, model, s = setup(name, dt)
+    u, r, Kcoh, _ = lip_state(prob, model, s, 51)
+    x_u, x_p = W.random_vectors(model.N, 52)
+    x_u = x_u.astype(np.float32).astype(np.float64)
+    x_p = x_p.astype(np.float32).astype(np.float64)
+    for op in ("KB", "KT", "A22"):
+        if op == "KT" and prob.kf is None:
+            continue
+        op_o = {"KB": "Kb", "KT": "KT", "A22": "A22"}[op]
+        yu_o, yp_o = osolve.apply(model, op_o, x_u.reshape(-1), x_p, dt=dt, Kcoh=Kcoh)
+        if op == "A22":
+            y = s.apply(op, cuda(x_p, torch.float32)).cpu().numpy()
+            assert rel(y, yp_o) < 5e-6, (op, rel(y, yp_o))
+        else:
+            y = s.apply(op, cuda(x_u, torch.float32)).cpu().numpy()
+            assert rel(y.reshape(-1), yu_o) < 5e-6, (op, rel(y.reshape(-1), yu_o))
+
+
 @pytest.mark.parametrize("name", ["box_tied_8", "ragged_tied", "sheared_x_untied", "no_fault"])
 def test_residual(name):
     dt = 1.3

@@ -75,7 +75,11 @@ def test_fault_input_errors_are_reported():
     """Invalid fault descriptions and out-of-order calls return status codes
     (GM_EINVAL = -1, GM_ESTATE = -7) through the binding as GMError, before any
     device work: a node in two pairs, a triangle naming a pair out of range,
-    t1_ref normal to the fault, a step before the fault is set, dt = 0."""
+    t1_ref normal to the fault, a step before the fault is set, dt = 0, and
+    fault descriptions whose triangle order or lip order would flip the pair
+    normal: one triangle reversed (an edge then runs the same way in two
+    triangles), every triangle reversed (normal from plus to minus), and the
+    lips of every pair swapped."""
     need_gpu()
     import paper_2410_17133_gb300 as gm
     prob = W.tetrahedralize(W.tiny_faulted(2, 2, 2))
@@ -100,6 +104,17 @@ def test_fault_input_errors_are_reported():
     with pytest.raises(gm.GMError) as e:
         s.fault(prob.pairs, prob.fault_tris, (0.0, 0.0, 1.0), prob.fault)
     assert e.value.code == -1
+    one = prob.fault_tris.copy()
+    one[0] = one[0, ::-1]
+    with pytest.raises(gm.GMError) as e:
+        s.fault(prob.pairs, one, prob.t1_ref, prob.fault)
+    assert e.value.code == -1 and "ordered inconsistently" in str(e.value)
+    with pytest.raises(gm.GMError) as e:
+        s.fault(prob.pairs, prob.fault_tris[:, ::-1].copy(), prob.t1_ref, prob.fault)
+    assert e.value.code == -1 and "side" in str(e.value)
+    with pytest.raises(gm.GMError) as e:
+        s.fault(prob.pairs[:, ::-1].copy(), prob.fault_tris, prob.t1_ref, prob.fault)
+    assert e.value.code == -1 and "side" in str(e.value)
     s.fault(prob.pairs, prob.fault_tris, prob.t1_ref, prob.fault)
     with pytest.raises(gm.GMError) as e:
         s.fault_step(0.0, u, p)

@@ -42,3 +42,27 @@ def test_residual_noalloc_matches_residual_twice():
         assert rel(b2, b1) < 1e-12
         assert abs(r_na.value - r_ref.value) <= 1e-12 * r_ref.value
         assert r_ref.value > 0
+
+
+def test_residual_noalloc_rejects_grids_beyond_its_scratch():
+    """257^3 nodes exceed the fixed scratch limit of 2^24 nodes: the call must
+    return GM_EINVAL (-1) with a message naming the limit, before any GPU
+    work, and leave the output untouched."""
+    need_gpu()
+    import paper_2410_17133_gb300 as gm
+    n = 256
+    s = gm.Solver(0)
+    s.mesh(n, n, n, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    s.materials(np.full(n ** 3, 20e9), 1e-15, 0.25, 0.8, 50e9, 1e-3)
+    s.bind()
+    assert s.N == (n + 1) ** 3 > 1 << 24
+    du = torch.zeros((3, s.N), dtype=torch.float64, device="cuda")
+    dp = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    b = torch.full((4, s.N), 7.0, dtype=torch.float64, device="cuda")
+    r = ctypes.c_double(-1.0)
+    rc = s._L.gm_residual_noalloc(s.h, ctypes.c_void_p(du.data_ptr()), ctypes.c_void_p(dp.data_ptr()),
+                                  ctypes.c_void_p(b.data_ptr()), ctypes.byref(r), None)
+    assert rc == -1
+    assert b"16777216" in s._L.gm_last_error(s.h)
+    assert torch.all(b == 7.0) and r.value == -1.0
+    s.close()
