@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="the first steps of the timed window, run again by the plain FP64 solver")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mesh", type=int, default=0, metavar="N",
+                    help="run the workload on an N^3 grid instead of its own size (profiling runs)")
     ap.add_argument("--apply-profile", type=int, default=0, metavar="N",
                     help="only run one K_b, K_T, J and A22 apply in FP32 and FP64 on the N^3 grid "
                          "of the workload, for kernel profiling; prints their times")
@@ -92,15 +94,17 @@ def run_apply_profile(n, config):
     print(json.dumps(out))
 
 
-def workload(name, steps=20):
+def workload(name, steps=20, n=0):
     import workloads as W
     if name == "inclined160":
-        return W.inclined_lognormal(n=160, steps=steps), {
-            "workload": "inclined-fault 160^3 Q1 hexes (16.8 M DoF), 60 deg fault, lognormal k "
-                        "(log10 N(-15, 0.5)), E ~ U[10, 30] GPa, constant injection, 5 s steps",
-            "mesh": [160, 160, 160], "seed": 3}
-    return W.slip_front(n=64, steps=max(steps, 50)), {
-        "workload": "slip-front 64^3 Q1 (Table 1 fault, ratio 0.99, T=0.1)", "mesh": [64, 64, 64]}
+        n = n or 160
+        return W.inclined_lognormal(n=n, steps=steps), {
+            "workload": f"inclined-fault {n}^3 Q1 hexes ({4 * (n + 1) ** 2 * (n + 2) / 1e6:.1f} M DoF), 60 deg "
+                        "fault, lognormal k (log10 N(-15, 0.5)), E ~ U[10, 30] GPa, constant injection, 5 s steps",
+            "mesh": [n, n, n], "seed": 3}
+    n = n or 64
+    return W.slip_front(n=n, steps=max(steps, 50)), {
+        "workload": f"slip-front {n}^3 Q1 (Table 1 fault, ratio 0.99, T=0.1)", "mesh": [n, n, n]}
 
 
 def sample_workload(name, n, steps=20):
@@ -227,7 +231,7 @@ def run_gm(args, rank, world, local_rank):
 
     W, K, F = args.warmup, args.steps, min(args.fp64_steps, args.steps)
     KE = min(K, 2)
-    prob, cfg = workload(args.config, steps=W + K + KE + 4)
+    prob, cfg = workload(args.config, steps=W + K + KE + 4, n=args.mesh)
     s = gm.Solver.from_problem(prob, device=local_rank)
     N = s.N
     ndof = 4 * N

@@ -288,7 +288,7 @@ static int gm_bulk32_launch(gm_ctx* c, BulkArgs<float>& b, cudaStream_t s)
     gm_bulk32_setup<CLS, MODE, PCG>(dev);
     const int resident = gm_bulk32_resident<CLS, MODE, PCG>(dev);
     const int gx = (c->nx + 1 + 14) / 15, gy = (c->ny + 1 + 14) / 15;
-    const int zc = gm_pick_zchunk(c, (long long)gx * gy, resident);
+    const int zc = std::min(gm_pick_zchunk(c, (long long)gx * gy, resident), gm32::MAXPL - 2);
     const int gz = (c->g.nplanes + zc - 1) / zc;
     b.zchunk = zc;
     gm_bulk32_kernel<CLS, MODE, PCG><<<dim3(gx, gy, gz), gm32::NT, SMEM, s>>>(b, c->R32p);
@@ -348,6 +348,7 @@ inline BulkArgs<T> gm_bulk_args(gm_ctx* c, double cK, double cApu, double cAup, 
     b.cS = T(cS / c->M);
     b.cC = T(cC);
     b.skip = nullptr;
+    b.tflag = c->dtflag.as<uint8_t>();
     b.zu = nullptr; b.zp = nullptr; b.pu_new = nullptr; b.pp_new = nullptr;
     b.beta = nullptr; b.part = nullptr;
     b.fs = nullptr; b.cFS = T(0);

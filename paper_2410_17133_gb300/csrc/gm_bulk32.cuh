@@ -36,7 +36,12 @@ constexpr int PLANE = TN * RS;         // floats per staged field plane
 constexpr int NS = 4;                  // ring stages
 constexpr int DA = 3;                  // planes staged ahead of the march
 constexpr int NSLOT = (TILE + NT - 1) / NT;
+constexpr int MAXPL = 512;             // staged planes per CTA at most (chunk + 2 halo planes)
 
+#ifndef GM32_PACKED
+#define GM32_PACKED 0
+#endif
+#if GM32_PACKED
 __device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -49,6 +54,36 @@ __device__ __forceinline__ float2 psub(float2 a, float2 b)
     float2 d;
     memcpy(&d, &rd, 8);
     return d;
+}
+#else
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c)
+{
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+}
+#endif
+// products with a duplicated constant coefficient: packed, or two scalar FMAs
+// that read the coefficient from the parameter bank
+#ifndef GM32_PACKED_PRODUCTS
+#define GM32_PACKED_PRODUCTS GM32_PACKED
+#endif
+__device__ __forceinline__ float2 pcfma(float2 k, float2 b, float2 c)
+{
+#if GM32_PACKED_PRODUCTS
+    return pfma(k, b, c);
+#else
+    return make_float2(fmaf(k.x, b.x, c.x), fmaf(k.x, b.y, c.y));
+#endif
+}
+__device__ __forceinline__ float2 pcmul(float2 k, float2 b)
+{
+#if GM32_PACKED_PRODUCTS
+    return pmul(k, b);
+#else
+    return make_float2(k.x * b.x, k.x * b.y);
+#endif
 }
 
 __device__ __forceinline__ void cp4(unsigned dst, const void* src, int bytes)
@@ -65,7 +100,7 @@ constexpr size_t smem_bytes()
     constexpr int NF = MODE == GM_M_K ? 3 : 1;
     constexpr int NIN = PCG ? 2 * NF : NF;
     return sizeof(float) * (size_t)NS * NIN * PLANE + sizeof(unsigned) * (size_t)NS * TILE +
-           sizeof(float) * 2 * NF * NT + sizeof(double) * 4;
+           sizeof(float) * 2 * NF * NT + sizeof(double) * 4 + MAXPL;
 }
 
 }  // namespace gm32
@@ -93,6 +128,7 @@ gm_bulk32_kernel(const BulkArgs<float> a, const __grid_constant__ RefPairs32 R)
     unsigned* s_mw = reinterpret_cast<unsigned*>(s_in + NS * NIN * PLANE); // [NS][TILE] mask words
     float* s_x = reinterpret_cast<float*>(s_mw + NS * TILE);              // [2][NF][NT]
     double* s_red = reinterpret_cast<double*>(s_x + 2 * NF * NT);         // [4]
+    uint8_t* s_flag = reinterpret_cast<uint8_t*>(s_red + 4);               // [MAXPL] constrained tile-planes
 
     const GridDesc& g = a.g;
     const int tid = threadIdx.x;
@@ -115,6 +151,14 @@ gm_bulk32_kernel(const BulkArgs<float> a, const __grid_constant__ RefPairs32 R)
     auto layer_exists = [&](int kb) -> bool { return kb >= 0 && kb + 1 < g.nplanes && kb != g.kf; };
     auto layer_index = [&](int kb) -> int { return (g.kf >= 0 && kb > g.kf) ? kb - 1 : kb; };
 
+    const int kbeg = (z0 > 0 && layer_exists(z0 - 1)) ? z0 - 1 : z0;
+    const int klast = (z1 < g.nplanes && layer_exists(z1 - 1)) ? z1 : z1 - 1;
+    for (int i = tid; i <= klast - kbeg; i += NT)
+        s_flag[i] = a.tflag != nullptr ? a.tflag[((kbeg + i) * (int)gridDim.y + (int)blockIdx.y) * (int)gridDim.x +
+                                                 (int)blockIdx.x]
+                                       : (uint8_t)1;
+    __syncthreads();
+
     // staged nodes of this thread: tile index tid + NT s
     int s_off[NSLOT], s_pos[NSLOT];
     bool s_in_grid[NSLOT];
@@ -134,6 +178,7 @@ gm_bulk32_kernel(const BulkArgs<float> a, const __grid_constant__ RefPairs32 R)
     // and for each node the aligned mask word holding its byte)
     auto stage = [&](int k) {
         const int st = k & (NS - 1);
+        const bool fl = s_flag[k - kbeg] != 0;
         const int pb = k * nb;
         // a tied upper lip reads the pressure (and its constraint) of the lower lip
         const int pbp = (!DO_K && g.tied && k == g.kf + 1) ? pb - nb : pb;
@@ -150,19 +195,21 @@ gm_bulk32_kernel(const BulkArgs<float> a, const __grid_constant__ RefPairs32 R)
                 if constexpr (PCG)
                     cp4(s_in_u + 4u * (unsigned)((st * NIN + NF + f) * PLANE + s_pos[s]), pin + f * N + nodec, bytes);
             }
-            cp4(s_mw_u + 4u * (unsigned)(st * TILE + tid + NT * s), a.mask + (nodec & ~3), bytes);
+            if (fl) cp4(s_mw_u + 4u * (unsigned)(st * TILE + tid + NT * s), a.mask + (nodec & ~3), bytes);
         }
     };
     // after the thread's own copies of plane k landed: constrained inputs to
     // zero, PCG mode forms z + beta p_old in place
     auto fixup = [&](int k) {
         const int st = k & (NS - 1);
+        const bool fl = s_flag[k - kbeg] != 0;
+        if (!PCG && !fl) return;
         const int pbp = (!DO_K && g.tied && k == g.kf + 1) ? (k - 1) * nb : k * nb;
 #pragma unroll
         for (int s = 0; s < NSLOT; ++s) {
             if (s_pos[s] < 0 || !s_in_grid[s]) continue;
             const int node = pbp + s_off[s];
-            const unsigned m = (s_mw[st * TILE + tid + NT * s] >> (8 * (node & 3))) & 0xffu;
+            const unsigned m = fl ? (s_mw[st * TILE + tid + NT * s] >> (8 * (node & 3))) & 0xffu : 0u;
             float* v = s_in + st * NIN * PLANE + s_pos[s];
             if constexpr (PCG) {
 #pragma unroll
@@ -205,6 +252,8 @@ gm_bulk32_kernel(const BulkArgs<float> a, const __grid_constant__ RefPairs32 R)
             tt[f][3] = psub(bm, tm);
             own_cur[f] = B0;
         }
+        m_cur = 0;
+        if (s_flag[k - kbeg] == 0) return;
         const int pb = k * nb + (y0 - 1 + r0) * rowlen + x0 - 1 + tx;
         const unsigned w0 = s_mw[st * TILE + r0 * TN + tx], w1 = s_mw[st * TILE + (r0 + 1) * TN + tx];
         // own mask words were staged by other threads at tile positions of
@@ -234,8 +283,8 @@ gm_bulk32_kernel(const BulkArgs<float> a, const __grid_constant__ RefPairs32 R)
 #pragma unroll
                 for (int j = 0; j < 24; ++j)
                     if (PP.k[c * 8 + s][j] >= 0 && (j & 7) != 0) {
-                        acc = first ? pmul(R.K[PP.k[c * 8 + s][j]], xv[j])
-                                    : pfma(R.K[PP.k[c * 8 + s][j]], xv[j], acc);
+                        acc = first ? pcmul(R.K[PP.k[c * 8 + s][j]], xv[j])
+                                    : pcfma(R.K[PP.k[c * 8 + s][j]], xv[j], acc);
                         first = false;
                     }
                 return acc;
@@ -257,7 +306,7 @@ gm_bulk32_kernel(const BulkArgs<float> a, const __grid_constant__ RefPairs32 R)
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
                     if (PP.l[s][j] >= 0) {
-                        acc = first ? pmul(R.L[PP.l[s][j]], xv[j]) : pfma(R.L[PP.l[s][j]], xv[j], acc);
+                        acc = first ? pcmul(R.L[PP.l[s][j]], xv[j]) : pcfma(R.L[PP.l[s][j]], xv[j], acc);
                         first = false;
                     }
                 acc = pmul(ce, acc);
@@ -317,8 +366,6 @@ gm_bulk32_kernel(const BulkArgs<float> a, const __grid_constant__ RefPairs32 R)
         pplane = -1;
     };
 
-    const int kbeg = (z0 > 0 && layer_exists(z0 - 1)) ? z0 - 1 : z0;
-    const int klast = (z1 < g.nplanes && layer_exists(z1 - 1)) ? z1 : z1 - 1;
 #pragma unroll
     for (int i = 0; i < DA; ++i) {
         if (kbeg + i <= klast) stage(kbeg + i);

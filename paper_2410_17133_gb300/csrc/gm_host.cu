@@ -960,6 +960,33 @@ int bind_impl(gm_ctx* c)
             if (c->fixed[f * N + n]) mask[n] |= (uint8_t)(1u << f);
     GM_CUDA_TRY(c, cudaMemcpy(c->dmask.p, mask.data(), N, cudaMemcpyHostToDevice));
     GM_CUDA_TRY(c, cudaMemset(static_cast<uint8_t*>(c->dmask.p) + N, 0, 64));
+    {
+        // constrained tile-planes of the FP32 bulk kernel (15 x 15 tiles, 17 x 17
+        // staged nodes; a tied upper lip also reads the lower lip's constraints)
+        const int gx = (c->nx + 1 + 14) / 15, gy = (c->ny + 1 + 14) / 15, np = c->g.nplanes;
+        const long long rl = c->nx + 1, nbp = c->g.nb;
+        std::vector<uint8_t> any(nbp * np, 0), tf((size_t)np * gx * gy, 0);
+        for (long long n = 0; n < N; ++n) any[n] = mask[n] != 0;
+        for (int k = 0; k < np; ++k)
+            for (int by = 0; by < gy; ++by)
+                for (int bx = 0; bx < gx; ++bx) {
+                    uint8_t f = 0;
+                    for (int j = by * 15 - 1; j <= by * 15 + 15 && !f; ++j) {
+                        if (j < 0 || j > c->ny) continue;
+                        for (int i = bx * 15 - 1; i <= bx * 15 + 15; ++i) {
+                            if (i < 0 || i > c->nx) continue;
+                            const long long q = i + rl * j;
+                            if (any[q + nbp * k] || (c->g.tied && k == c->g.kf + 1 && any[q + nbp * c->g.kf])) {
+                                f = 1;
+                                break;
+                            }
+                        }
+                    }
+                    tf[((size_t)k * gy + by) * gx + bx] = f;
+                }
+        GM_CUDA_TRY(c, c->dtflag.alloc(tf.size()));
+        GM_CUDA_TRY(c, cudaMemcpy(c->dtflag.p, tf.data(), tf.size(), cudaMemcpyHostToDevice));
+    }
     c->bound = true;   // loads upload below needs the grid
     int rc = gm_prepare_bulk32(c);
     if (rc) { c->bound = false; return rc; }

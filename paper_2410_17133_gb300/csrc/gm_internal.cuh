@@ -191,6 +191,10 @@ struct BulkArgs {
     const uint8_t* mask;
     T cK, cApu, cAup, cS, cC;   // alpha and 1/M folded in by the host
     const int* skip; // if non-null and *skip != 0 the kernel returns at once
+    // FP32 kernel: per (node plane, 15 x 15 tile) 1 if a node of the tile's
+    // staged 17 x 17 region carries a constraint (for a tied upper lip, also of
+    // the lower lip it reads); null: every tile-plane is treated as constrained
+    const uint8_t* tflag;
     // PCG mode: input p = z + beta * x (x = p_old), p written to p*_new,
     // per-CTA partial of p.(A p) over non-lip nodes written to part[cta]
     const T* zu;
@@ -430,6 +434,7 @@ struct gm_ctx {
     DevBuf dFS64, dFS32, dAfsinv64, dAfsinv32;         // fixed-stress storage term
     DevBuf dscal;                                      // PcgScalars[4] + misc
     DevBuf dpart;                                      // reduction partials
+    DevBuf dtflag;                                     // constrained tile-planes of the FP32 bulk kernel
     DevBuf dcount;                                     // last-block counters
     // work vectors (FP64)
     DevBuf w_du, w_dp, w_ut, w_pt, w_b, w_x, w_y1u, w_y1p, w_y2u, w_y2p;

@@ -31,7 +31,7 @@ namespace {
 constexpr int MG_MAX_LEVELS = 8;
 constexpr int MG_SMOOTH_DEG = 2;
 constexpr int MG_MAX_COARSE_DEG = 32;
-// tuning (environment, read at build): coarse grids keep at least
+// tuning (environment, read at set-up): coarse grids keep at least
 // GM_MG_MIN_CELLS cells per direction (default 2); the coarsest level runs a
 // Chebyshev polynomial of degree GM_MG_COARSE_DEG (default 8)
 int mg_min_cells()
@@ -39,6 +39,13 @@ int mg_min_cells()
     const char* v = std::getenv("GM_MG_MIN_CELLS");
     const int n = v ? std::atoi(v) : 2;
     return n >= 1 ? n : 2;
+}
+// smoothing degree of the other levels: GM_MG_SMOOTH_DEG (default 2)
+int mg_smooth_deg()
+{
+    const char* v = std::getenv("GM_MG_SMOOTH_DEG");
+    const int n = v ? std::atoi(v) : MG_SMOOTH_DEG;
+    return (n >= 1 && n <= MG_MAX_COARSE_DEG) ? n : MG_SMOOTH_DEG;
 }
 int mg_coarse_deg()
 {
@@ -594,7 +601,7 @@ int build(gm_ctx* c)
     for (size_t l = 0; l < c->mg.size(); ++l) {
         MGLevel& L = c->mg[l];
         const bool last = l + 1 == c->mg.size();
-        L.deg = last ? mg_coarse_deg() : MG_SMOOTH_DEG;
+        L.deg = last ? mg_coarse_deg() : mg_smooth_deg();
         L.coef_off = off;
         const double hi = 1.15 * L.lmax;
         cheb_coefs(last ? 0.01 * hi : 0.25 * L.lmax, hi, L.deg, coef);
