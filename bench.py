@@ -41,6 +41,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "operator-apply GDoF/s & s per implicit step, FP32-refined vs FP64, at 1e-8 resid"
 NEWTON_RTOL = 1e-8
+# inexact Newton: inner PCG and outer partitioned-CG tolerances of both arms
+# (the FP64 Newton loop refines; Newton iterations are set by the fault law)
+INNER_RTOL, OUTER_RTOL = 1e-2, 1e-1
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 FALLBACK_HBM = 6800.0
@@ -249,7 +252,8 @@ def run_gm(args, rank, world, local_rank):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            rep = solver.step(prob.dts[k], newton_rtol=NEWTON_RTOL, precision=precision, stream=stream)
+            rep = solver.step(prob.dts[k], newton_rtol=NEWTON_RTOL, precision=precision, inner_rtol=INNER_RTOL,
+                              outer_rtol=OUTER_RTOL, stream=stream)
             b.record(stream)
             b.synchronize()
             ms.append(a.elapsed_time(b))
@@ -302,7 +306,8 @@ def run_gm(args, rank, world, local_rank):
                 "inner_a": [r["inner_a"] for r in r64],
                 "rel_l2_u_vs_fp32_refined": du, "rel_l2_p_vs_fp32_refined": dp,
                 "flags_equal": bool(np.array_equal(c32["flags"], b64["flags"])),
-                "preconditioners": "same as the FP32-refined solver (multigrid K_T, Jacobi A22), in FP64"}
+                "preconditioners": "same as the FP32-refined solver (multigrid K_T, Jacobi A22), in FP64",
+                "tolerances": f"the same as the FP32-refined solver: inner {INNER_RTOL}, outer {OUTER_RTOL}, Newton {NEWTON_RTOL}"}
 
     # operator applies: median of 20 launches each, L2 flushed between them
     def apply_time(which, x, y, reps=20):
@@ -375,7 +380,8 @@ def run_gm(args, rank, world, local_rank):
     t0 = time.perf_counter()
     for k in range(W + K, W + K + KE):
         s.set_state(u=pin["u"].numpy(), p=pin["p"].numpy(), dlie=pin["dlie"].numpy(), flags=pin["flags"].numpy())
-        s.step(prob.dts[k], newton_rtol=NEWTON_RTOL, precision=gm.F32, stream=stream)
+        s.step(prob.dts[k], newton_rtol=NEWTON_RTOL, precision=gm.F32, inner_rtol=INNER_RTOL, outer_rtol=OUTER_RTOL,
+               stream=stream)
         a = s.get_state()
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
@@ -394,7 +400,7 @@ def run_gm(args, rank, world, local_rank):
             "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32-refined (f32 operators/preconditioners; f64 residual, dots, return map)",
             "data": "synthetic (seeded workload restating the paper's set-up; no paper meshes)",
-            "config": dict(cfg, dofs=ndof, newton_rtol=NEWTON_RTOL,
+            "config": dict(cfg, dofs=ndof, newton_rtol=NEWTON_RTOL, inner_rtol=INNER_RTOL, outer_rtol=OUTER_RTOL,
                            steps_timed=f"{W}..{W + K - 1} of the schedule",
                            l2="flushed (512 MB write) between timed steps and between timed applies",
                            inner_solvers="K_T: PCG with a geometric multigrid V-cycle; A22: Jacobi PCG; "

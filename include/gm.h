@@ -88,9 +88,10 @@ typedef struct {
 typedef struct {
     double newton_rtol;      /* Newton stop: rhat <= rtol * max(rhat0, 1e-3 shat) */
     int newton_maxit;        /* Newton iteration limit */
-    double outer_rtol;       /* partitioned CG relative tolerance */
+    double outer_rtol;       /* partitioned CG relative tolerance (defaults: 1e-8 FP64, 1e-1 FP32) */
     int outer_maxit;
-    double inner_rtol;       /* inner PCG relative tolerance (K_T and A22 solves) */
+    double inner_rtol;       /* inner PCG relative tolerance (K_T and A22 solves; defaults: 1e-10
+                                FP64, 1e-2 FP32: the Newton loop refines inexact solves) */
     int inner_maxit;
     int precision;           /* GM_F64, or GM_F32: FP32 operators + preconditioners
                                 inside the FP64 Newton/refinement loop */

@@ -327,8 +327,8 @@ class Solver:
                 and schur_precond == 0):
             opts = None
         else:
-            d_outer = 1e-8 if precision == F64 else 1e-4
-            d_inner = 1e-10 if precision == F64 else 1e-5
+            d_outer = 1e-8 if precision == F64 else 1e-1
+            d_inner = 1e-10 if precision == F64 else 1e-2
             opts = StepOpts(1e-10 if newton_rtol is None else newton_rtol, newton_maxit,
                             d_outer if outer_rtol is None else outer_rtol, outer_maxit,
                             d_inner if inner_rtol is None else inner_rtol, inner_maxit, precision,

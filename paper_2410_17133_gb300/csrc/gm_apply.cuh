@@ -291,7 +291,11 @@ static int gm_bulk32_launch(gm_ctx* c, BulkArgs<float>& b, cudaStream_t s)
     const int zc = std::min(gm_pick_zchunk(c, (long long)gx * gy, resident), gm32::MAXPL - 2);
     const int gz = (c->g.nplanes + zc - 1) / zc;
     b.zchunk = zc;
+#if GM32_PACKED_PRODUCTS
     gm_bulk32_kernel<CLS, MODE, PCG><<<dim3(gx, gy, gz), gm32::NT, SMEM, s>>>(b, c->R32p);
+#else
+    gm_bulk32_kernel<CLS, MODE, PCG><<<dim3(gx, gy, gz), gm32::NT, SMEM, s>>>(b, c->R32);
+#endif
     return gx * gy * gz;
 }
 

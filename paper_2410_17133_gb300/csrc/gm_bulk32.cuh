@@ -85,6 +85,21 @@ __device__ __forceinline__ float2 pcmul(float2 k, float2 b)
     return make_float2(k.x * b.x, k.x * b.y);
 #endif
 }
+// scalar coefficient (the FP32 parameter block without duplication)
+__device__ __forceinline__ float2 pcfma(float k, float2 b, float2 c)
+{
+    return make_float2(fmaf(k, b.x, c.x), fmaf(k, b.y, c.y));
+}
+__device__ __forceinline__ float2 pcmul(float k, float2 b) { return make_float2(k * b.x, k * b.y); }
+__device__ __forceinline__ float2 dup(float k) { return make_float2(k, k); }
+__device__ __forceinline__ float2 dup(float2 k) { return k; }
+
+// kernel parameter block of the pattern coefficients
+#if GM32_PACKED_PRODUCTS
+using Ref32 = RefPairs32;
+#else
+using Ref32 = RefOps<float>;
+#endif
 
 __device__ __forceinline__ void cp4(unsigned dst, const void* src, int bytes)
 {
@@ -111,7 +126,7 @@ constexpr int gm32_min_blocks() { return MODE == GM_M_K ? 3 : 4; }
 
 template <int CLS, int MODE, bool PCG>
 __global__ void __launch_bounds__(gm32::NT, gm32_min_blocks<MODE>())
-gm_bulk32_kernel(const BulkArgs<float> a, const __grid_constant__ RefPairs32 R)
+gm_bulk32_kernel(const BulkArgs<float> a, const __grid_constant__ gm32::Ref32 R)
 {
     using namespace gm32;
     constexpr bool DO_K = MODE == GM_M_K;
@@ -310,7 +325,7 @@ gm_bulk32_kernel(const BulkArgs<float> a, const __grid_constant__ RefPairs32 R)
                         first = false;
                     }
                 acc = pmul(ce, acc);
-                return pfma(pmul(cs, R.M[s]), xv[s], acc);
+                return pfma(pmul(cs, dup(R.M[s])), xv[s], acc);
             };
 #pragma unroll
             for (int q = 0; q < 4; ++q) {

@@ -140,3 +140,49 @@ def test_fullsize_slip_front_matches_closed_form():
         assert abs(R - lam * La) / (lam * La) < 0.05, (t, R, lam * La)
         checked += 1
     assert checked >= 5
+
+
+def test_marginally_pressurised_rupture_matches_lambda_4():
+    """The marginally pressurised case of Sec. 4.2 (tau0 = 47.830 MPa, Q = 1e-6
+    m^3/s: T = 4) on 256^3 hexes of the 40 m cube through its 64 geometric steps
+    (FP32-refined, Newton 1e-8).  The rupture stays far behind the pressure
+    front, R = lambda(4) L with lambda(4) = 0.1387.  Once the rupture spans
+    several cells (R >= 5 cells), the pressure front L (p = dp* E1(1) on the
+    fault, interpolated along a grid line through the injection point) must be
+    within the paper's 8 % of sqrt(4 D t) and the rupture radius within its 5 %
+    of lambda(4) sqrt(4 D t).  The rupture radius is taken from the slipping
+    area, R = h sqrt(n_slip / pi): the farthest slipping node would quantise R
+    to whole cells (11 % of R at the end)."""
+    import math
+    from oracle import analytic as A
+    need_gpu()
+    n = 256
+    prob = W.marginally_pressurised(n=n)
+    s = solver_for(prob)
+    fp = prob.fault
+    D = A.fault_diffusivity(fp.wk_par, fp.MF, prob.mu_f, fp.w0)
+    dps = A.theis_dpstar(prob.fp.sum(), prob.mu_f, fp.wk_par)
+    lam = A.lambda_of_T(A.stress_injection_parameter(fp.tau0[0], fp.f, fp.tn0, prob.fp.sum(), prob.mu_f, fp.wk_par))
+    assert abs(lam - 0.1387) < 1e-3
+    h = prob.h[0]
+    nb = (n + 1) ** 2
+    t = 0.0
+    checked = 0
+    for dt in prob.dts:
+        s.step(dt, newton_rtol=1e-8, precision=1)
+        t += dt
+        st = s.get_state()
+        nslip = int((st["flags"] == 2).sum())
+        R = h * math.sqrt(nslip / math.pi)
+        if R < 5 * h:
+            continue
+        p = st["p"][prob.kf * nb:(prob.kf + 1) * nb]
+        row = p.reshape(n + 1, n + 1)[n // 2, n // 2:]
+        target = dps * 0.21938393439552          # E1(1)
+        i = int(np.where(row < target)[0][0])
+        L = h * (i - 1 + (row[i - 1] - target) / (row[i - 1] - row[i]))
+        La = math.sqrt(4 * D * t)
+        assert abs(L - La) / La < 0.08, (t, L, La)
+        assert abs(R - lam * La) / (lam * La) < 0.05, (t, R, lam * La, nslip)
+        checked += 1
+    assert checked >= 3
