@@ -174,7 +174,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("gm_bulk32.cuh", "gm_apply.cuh", "gm_internal.cuh"):
+    for f in ("gm_bulk32.cuh", "gm_apply.cuh"):
         with open(os.path.join(ROOT, "paper_2410_17133_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -928,6 +928,7 @@ int bind_impl(gm_ctx* c)
         {&c->a_pb32, (size_t)N * 4},
         {&c->a_q32, (size_t)N * 4}, {&c->a_x32, (size_t)N * 4}, {&c->a_b32, (size_t)N * 4},
         {&c->o_y1, (size_t)N3 * 8}, {&c->o_w, (size_t)N3 * 8}, {&c->o_t3, (size_t)N3 * 8},
+        {&c->o_s32a, (size_t)N3 * 4}, {&c->o_s32b, (size_t)N3 * 4},
         {&c->o_r, (size_t)N * 8}, {&c->o_z, (size_t)N * 8}, {&c->o_zold, (size_t)N * 8},
         {&c->o_p, (size_t)N * 8}, {&c->o_q, (size_t)N * 8}, {&c->o_t1, (size_t)N * 8},
     };

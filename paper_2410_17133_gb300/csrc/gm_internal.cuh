@@ -445,6 +445,7 @@ struct gm_ctx {
     int bulk_grid = 0;                                 // CTAs of one bulk apply
     int zchunk_override = 0;                           // GM_BULK_ZCHUNK (tuning), 0 = heuristic
     DevBuf o_y1, o_w, o_x1, o_t3, o_r, o_z, o_zold, o_p, o_q, o_x2, o_t1;   // outer CG
+    DevBuf o_s32a, o_s32b;                             // FP32 operands / products of the outer CG (3N each)
     DevBuf dprevstate;
     void* hpin = nullptr;                              // pinned host scratch (4 KB)
     // CUDA graphs of two fused PCG iterations, per (operator, precision);

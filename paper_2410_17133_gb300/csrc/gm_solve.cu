@@ -196,6 +196,43 @@ static int dot2(gm_ctx* c, long long n, const double* x, const double* y, const 
     return GM_OK;
 }
 
+// Products of the outer iteration.  In FP32-refined solves (prec GM_F32) the
+// outer CG only has to reach its loose tolerance before the FP64 Newton
+// residual refines, so its operator products run in FP32 (operands cast to FP32
+// once, products cast back); dot products and vector updates stay FP64.
+namespace {
+struct OuterOps {
+    gm_ctx* c;
+    int prec;
+    cudaStream_t s;
+    float* a32;
+    float* b32;
+    // t3 (3N) = A_pu p ; the FP32 copy of p stays in a32[0, N) for a22()
+    int apu(const double* p, double* t3) {
+        if (prec == GM_F64) return gm_launch_apply_f64(c, GM_MODE_APU, 0, 1, 0, 0, 0, nullptr, p, t3, nullptr, s, nullptr);
+        int rc = gm_launch_copy_cast_d2f(c, c->N, p, a32, s);
+        if (!rc) rc = gm_launch_apply_f32(c, GM_MODE_APU, 0, 1, 0, 0, 0, nullptr, a32, b32, nullptr, s, nullptr);
+        if (!rc) rc = gm_launch_copy_cast_f2d(c, 3 * c->N, b32, t3, s);
+        return rc;
+    }
+    // q (N) = A22 p, p as given to the last apu() call
+    int a22(const double* p, double* q) {
+        if (prec == GM_F64) return gm_launch_apply_f64(c, GM_MODE_A22, 0, 0, 0, 1, c->dt, nullptr, p, nullptr, q, s, nullptr);
+        int rc = gm_launch_apply_f32(c, GM_MODE_A22, 0, 0, 0, 1, c->dt, nullptr, a32, nullptr, b32, s, nullptr);
+        if (!rc) rc = gm_launch_copy_cast_f2d(c, c->N, b32, q, s);
+        return rc;
+    }
+    // t1 (N) = A_up w
+    int aup(const double* w, double* t1) {
+        if (prec == GM_F64) return gm_launch_apply_f64(c, GM_MODE_AUP, 0, 0, 1, 0, 0, w, nullptr, nullptr, t1, s, nullptr);
+        int rc = gm_launch_copy_cast_d2f(c, 3 * c->N, w, a32, s);
+        if (!rc) rc = gm_launch_apply_f32(c, GM_MODE_AUP, 0, 0, 1, 0, 0, a32, nullptr, nullptr, b32, s, nullptr);
+        if (!rc) rc = gm_launch_copy_cast_f2d(c, c->N, b32, t1, s);
+        return rc;
+    }
+};
+}  // namespace
+
 // Prevost's partitioned CG on [K_T, -A_pu; A_up, A22] [x1; x2] = [b1; b2]:
 //   y1 = K_T^-1 b1,  r = b2 - A_up y1          (right side of Eq. schur_system)
 //   CG on S~ = A22 + A_up K_T^-1 A_pu, preconditioned by A22^-1, from x2 = 0
@@ -221,11 +258,12 @@ int gm_prevost(gm_ctx* c, int prec, const double* b1, const double* b2, double* 
     double* q = c->o_q.as<double>();
     double* t1 = c->o_t1.as<double>();
     long long ik = 0, ia = 0;
+    OuterOps ops{c, prec == GM_F64 ? GM_F64 : GM_F32, s, c->o_s32a.as<float>(), c->o_s32b.as<float>()};
 
     rc = gm_pcg(c, 0, prec, b1, y1, inner_rtol, inner_maxit, &it_in, nullptr, s, true);
     if (rc && rc != GM_ENOCONV) return rc;
     ik += it_in;
-    if ((rc = gm_launch_apply_f64(c, GM_MODE_AUP, 0, 0, 1, 0, 0, y1, nullptr, nullptr, t1, s, nullptr))) return rc;
+    if ((rc = ops.aup(y1, t1))) return rc;
     GM_CUDA_TRY(c, cudaMemcpyAsync(r, b2, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if ((rc = gm_launch_axpby(c, N, -1.0, t1, 1.0, r, s))) return rc;
     GM_CUDA_TRY(c, cudaMemsetAsync(x2, 0, N * sizeof(double), s));
@@ -246,12 +284,12 @@ int gm_prevost(gm_ctx* c, int prec, const double* b1, const double* b2, double* 
             return c->set_err(GM_ENOCONV, "partitioned CG: iteration limit");
         }
         // w = K_T^-1 A_pu p ;  q = A22 p + A_up w
-        if ((rc = gm_launch_apply_f64(c, GM_MODE_APU, 0, 1, 0, 0, 0, nullptr, p, t3, nullptr, s, nullptr))) return rc;
+        if ((rc = ops.apu(p, t3))) return rc;
         rc = gm_pcg(c, 0, prec, t3, w, inner_rtol, inner_maxit, &it_in, nullptr, s, true);
         if (rc && rc != GM_ENOCONV) return rc;
         ik += it_in;
-        if ((rc = gm_launch_apply_f64(c, GM_MODE_A22, 0, 0, 0, 1, c->dt, nullptr, p, nullptr, q, s, nullptr))) return rc;
-        if ((rc = gm_launch_apply_f64(c, GM_MODE_AUP, 0, 0, 1, 0, 0, w, nullptr, nullptr, t1, s, nullptr))) return rc;
+        if ((rc = ops.a22(p, q))) return rc;
+        if ((rc = ops.aup(w, t1))) return rc;
         if ((rc = gm_launch_axpby(c, N, 1.0, t1, 1.0, q, s))) return rc;
         if ((rc = dot2(c, N, p, q, nullptr, nullptr, d, s))) return rc;
         const double pq = d[0];
