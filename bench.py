@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="the first steps of the timed window, run again by the plain FP64 solver")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tet", action="store_true", help="skip the timed tetrahedral lines")
     ap.add_argument("--mesh", type=int, default=0, metavar="N",
                     help="run the workload on an N^3 grid instead of its own size (profiling runs)")
     ap.add_argument("--apply-profile", type=int, default=0, metavar="N",
@@ -390,6 +391,11 @@ def run_gm(args, rank, world, local_rank):
            "d2h_bytes_per_step": int(d2h), "ms_per_step": te / KE * 1e3, "steps": KE}
     log("e2e done")
 
+    tet = None
+    if rank == 0 and not args.no_tet:
+        tet = tet_lines()
+        log("tet lines done")
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.config)
@@ -406,7 +412,7 @@ def run_gm(args, rank, world, local_rank):
                            inner_solvers="K_T: PCG with a geometric multigrid V-cycle; A22: Jacobi PCG; "
                                          "the FP64 comparison uses the same preconditioners in FP64",
                            parallelism=f"replicas{world}" if world > 1 else "single"),
-            "roofline": roof, "apply": apply, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "apply": apply, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e, "tet": tet,
             "clocks": clocks, "gpu_launches": int(launches),
             "launches_per_step": launches / K, "bulk_applies_per_step": (ap1 - ap0) / K,
             "per_step": [{"ms": m, "newton": r["newton"], "outer": r["outer"], "inner_k": r["inner_k"],
@@ -418,6 +424,60 @@ def run_gm(args, rank, world, local_rank):
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# Tetrahedral path (P1 tets): timed Cryer steps and fault steps
+# ---------------------------------------------------------------------------
+def tet_lines(n_cryer=16, n_fault=8, fault_steps=2):
+    """Per-step times of the tetrahedral path: Cryer's octant (Sec. 4.1, FP64
+    partitioned CG) and the faulted cube of tets (Sec. 3.1, Newton with the
+    return map), the latter in FP64 and FP32-refined over the same steps."""
+    import numpy as np
+    import torch
+    import paper_2410_17133_gb300 as gm
+    import workloads as W
+    out = {}
+    prob = W.cryer_octant(n=n_cryer, steps=8)
+    s = gm.TetSolver.from_problem(prob)
+    u = torch.zeros((3, s.N), dtype=torch.float64, device="cuda")
+    p = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    s.step(prob.dts[0], u, p, rtol=1e-10)           # warm-up (preconditioner set-up)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its = [s.step(dt, u, p, rtol=1e-10)["iterations"] for dt in prob.dts[1:]]
+    torch.cuda.synchronize()
+    out["cryer"] = {"mesh": f"octant, {n_cryer}^3 cells x 6 tets", "nodes": s.N, "tets": s.M,
+                    "ms_per_step": (time.perf_counter() - t0) / len(its) * 1e3, "steps": len(its),
+                    "outer_per_step": float(np.mean(its)), "rtol": 1e-10, "precision": "f64"}
+    del s
+    fprob = W.tetrahedralize(W.fault_small(n_fault, steps=fault_steps + 1))
+    res = {}
+    for tag, prec in (("fp64", gm.F64), ("fp32_refined", gm.F32)):
+        s = gm.TetFaultSolver.from_problem(fprob)
+        u = torch.zeros((3, s.N), dtype=torch.float64, device="cuda")
+        p = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+        s.fault_step(fprob.dts[0], u, p, newton_rtol=1e-10, precision=prec)     # warm-up step
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = [s.fault_step(dt, u, p, newton_rtol=1e-10, precision=prec) for dt in fprob.dts[1:fault_steps + 1]]
+        torch.cuda.synchronize()
+        res[tag] = {"ms_per_step": (time.perf_counter() - t0) / fault_steps * 1e3,
+                    "newton": [r["newton"] for r in reps], "outer": [r["outer"] for r in reps],
+                    "inner_k": [r["inner_k"] for r in reps], "slip": [r["n_slip"] for r in reps],
+                    "u": u.cpu().numpy(), "p": p.cpu().numpy()}
+        del s
+    a, b = res["fp64"], res["fp32_refined"]
+    agree_u = float(np.linalg.norm(b["u"] - a["u"]) / max(np.linalg.norm(a["u"]), 1e-300))
+    agree_p = float(np.linalg.norm(b["p"] - a["p"]) / max(np.linalg.norm(a["p"]), 1e-300))
+    for r in res.values():
+        r.pop("u")
+        r.pop("p")
+    out["fault"] = dict(mesh=f"faulted cube, {n_fault}^3 hexes x 6 tets", newton_rtol=1e-10,
+                        steps=f"1..{fault_steps} of the schedule", **res,
+                        speedup_fp32_refined=a["ms_per_step"] / b["ms_per_step"],
+                        rel_diff_u=agree_u, rel_diff_p=agree_p)
+    return out
 
 
 # ---------------------------------------------------------------------------

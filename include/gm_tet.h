@@ -69,7 +69,7 @@ int gm_tet_surface_load(gm_tet* t, const int64_t* tris_host, int64_t n_tris, dou
  * Solved by Prevost's partitioned CG (Sec. 3.3.2): CG on the Schur complement
  * (S + dt C) + A^T K^-1 A, preconditioned by the diagonal of S + dt C,
  * relative tolerance rtol; inner K solves by PCG with 3x3 nodal block Jacobi
- * to rtol/100.  FP64.  report: outer iterations and final relative residual.
+ * to rtol/100, their scalars kept on the device.  FP64.  report: outer iterations and final relative residual.
  * GM_ENOCONV if an iteration limit (maxit) is reached.  Synchronises. */
 int gm_tet_step(gm_tet* t, double dt, double* u_dev, double* p_dev, double rtol, int maxit,
                 gm_solve_report* report_host, void* stream);
@@ -115,14 +115,20 @@ int gm_tet_fault_apply(gm_tet* t, int which, const double* x_dev, double* y_dev,
 /* One implicit step with the fault (Sec. 3.3.1): Newton on the incremental
  * residuals with the contact / Coulomb return map at every pair (Sec. 2.2.1),
  * each correction by Prevost's partitioned CG (Sec. 3.3.2) with inner K_T
- * solves by PCG with nodal 3x3 block Jacobi (the blocks include the pair's
- * cohesive tangent) and the diagonal of S + dt C as the outer preconditioner.
+ * solves by PCG preconditioned with nodal 3x3 block Jacobi off the fault and,
+ * for the two lips of each pair, the inverse of their 6x6 block (bulk blocks
+ * plus the cohesive tangent that couples them), and the diagonal of S + dt C
+ * as the outer preconditioner.  The inner PCG keeps its scalars on the device
+ * (no host round trip per dot product).
  * Stops when the fault states of two successive iterations agree and
  * rhat <= newton_rtol * max(rhat0, 1e-3 shat), with rhat the residual scaled
  * by the diagonals of K and S + dt C.  u_dev (3N) and p_dev (N) hold the
  * accepted state on entry and the new one on return (tied plus lips carry
  * their partner's pressure).  Uses newton_rtol, newton_maxit, outer_rtol,
- * outer_maxit, inner_rtol and inner_maxit of opts (FP64 only).  GM_ENEWTON
+ * outer_maxit, inner_rtol, inner_maxit and precision of opts: GM_F64, or
+ * GM_F32 for inner K_T solves in FP32 (operator, preconditioner blocks and
+ * vectors; the residuals, the return map and the outer CG stay FP64, and
+ * Newton refines the inexact corrections to newton_rtol).  GM_ENEWTON
  * at the Newton limit, GM_ENOCONV at a CG limit; the state is then unchanged.
  * Synchronises. */
 int gm_tet_fault_step(gm_tet* t, double dt, double* u_dev, double* p_dev, const gm_step_opts* opts_host,

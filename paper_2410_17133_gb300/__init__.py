@@ -579,10 +579,17 @@ class TetFaultSolver(TetSolver):
         self._chk(self._L.gm_tet_fault_apply(self.h, w, _tptr(x), _tptr(y), float(dt), _stream_ptr(stream)))
         return y
 
-    def fault_step(self, dt, u, p, newton_rtol=1e-12, newton_maxit=50, outer_rtol=1e-11, outer_maxit=5000,
-                   inner_rtol=1e-13, inner_maxit=20000, stream=None):
-        """gm_tet_fault_step: u (3, N), p (N,) float64 CUDA tensors updated in place."""
-        o = StepOpts(newton_rtol, newton_maxit, outer_rtol, outer_maxit, inner_rtol, inner_maxit, F64, 0)
+    def fault_step(self, dt, u, p, newton_rtol=1e-12, newton_maxit=50, outer_rtol=None, outer_maxit=5000,
+                   inner_rtol=None, inner_maxit=20000, precision=F64, stream=None):
+        """gm_tet_fault_step: u (3, N), p (N,) float64 CUDA tensors updated in place.
+        precision F32 runs the inner K_T solves in FP32 inside the FP64 Newton
+        loop; the tolerances default to 1e-11 / 1e-13 (outer / inner) in FP64
+        and to 1e-1 / 1e-2 in FP32, where Newton refines the inexact solves."""
+        if outer_rtol is None:
+            outer_rtol = 1e-11 if precision == F64 else 1e-1
+        if inner_rtol is None:
+            inner_rtol = 1e-13 if precision == F64 else 1e-2
+        o = StepOpts(newton_rtol, newton_maxit, outer_rtol, outer_maxit, inner_rtol, inner_maxit, precision, 0)
         rep = StepReport()
         self._chk(self._L.gm_tet_fault_step(self.h, float(dt), _tptr(u), _tptr(p), C.byref(o), C.byref(rep),
                                             _stream_ptr(stream)))

@@ -120,12 +120,14 @@ constexpr size_t smem_bytes()
 
 }  // namespace gm32
 
-// resident CTAs per SM the register allocation must allow
-template <int MODE>
-constexpr int gm32_min_blocks() { return MODE == GM_M_K ? 3 : 4; }
+// CTAs per SM the register budget is sized for: the elasticity product that
+// also writes the PCG direction gets the budget of 2 CTAs, where it runs
+// without spills (at 3 it spilled and ran about 3x slower than the plain one)
+template <int MODE, bool PCG>
+constexpr int gm32_min_blocks() { return MODE == GM_M_K ? (PCG ? 2 : 3) : 4; }
 
 template <int CLS, int MODE, bool PCG>
-__global__ void __launch_bounds__(gm32::NT, gm32_min_blocks<MODE>())
+__global__ void __launch_bounds__(gm32::NT, gm32_min_blocks<MODE, PCG>())
 gm_bulk32_kernel(const BulkArgs<float> a, const __grid_constant__ gm32::Ref32 R)
 {
     using namespace gm32;

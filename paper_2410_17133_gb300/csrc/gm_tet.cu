@@ -35,8 +35,9 @@ struct TetCoef {
 template <typename T, int MODE>
 __global__ void __launch_bounds__(128) gm_tet_apply_kernel(int N, const int* rowptr, const int* adj, const int* tets,
                                                            const T* G, const T* V, TetCoef<T> c, const T* xu,
-                                                           const T* xp, T* yu, T* yp)
+                                                           const T* xp, T* yu, T* yp, const int* skip)
 {
+    if (skip != nullptr && *skip != 0) return;
     constexpr bool IN_U = (MODE & (TM_K | TM_AUP)) != 0;
     constexpr bool IN_P = (MODE & (TM_APU | TM_S | TM_C)) != 0;
     constexpr bool OUT_U = (MODE & (TM_K | TM_APU)) != 0;
@@ -131,6 +132,8 @@ struct DBuf {
 
 }  // namespace
 
+#include "gm_tet_pcg.cuh"
+
 // Largest node, tetrahedron or fault-triangle count: all device index arithmetic
 // (12 gradients per element, 9 frame entries per pair, 3N field offsets) is in
 // 32-bit int, which this bound keeps in range.
@@ -151,7 +154,8 @@ struct gm_tet {
     std::vector<uint8_t> fixed;            // 4N: constrained (ux, uy, uz, p)
     std::vector<double> fu;                // 3N nodal forces
     DBuf mask, dfu, Kinv, Sd, Cd, part;
-    DBuf w[14];
+    DBuf w[15];
+    DBuf pcg_st, pcg_part;                  // device-resident PCG: state and reduction partials
     bool prec_ready = false;
     // fault: interface elements on the fault triangles
     bool has_fault = false, tied = false, fault_ready = false;
@@ -164,8 +168,29 @@ struct gm_tet {
     DBuf f_pm, f_pp, f_n2p, f_area, f_fr, f_Lt, f_tri, f_prow, f_padj;
     DBuf f_dlie_n, f_dlie, f_state, f_T, f_D, f_tn, f_F, f_dn, f_gs, f_flags_acc, f_gs_acc;
     DBuf f_Kblk, f_Kinv, f_fu, f_fpv, f_Sd, f_Cd, f_dKm, f_invdK, f_dAm, f_invdA, f_mask, f_err;
-    DBuf fw[24];
+    DBuf f_Pinv;                            // 36P: inverses of the lip-pair 6x6 blocks of K_T
+    DBuf f_Kinv32, f_Pinv32, f_D32;         // FP32 copies for the FP32 inner solves
+    DBuf fw[25];
+    DBuf fw32[5];                           // 3N floats each: x, r, z, p, q of the FP32 inner solves
     double f0sq = 0.0;
+    // captured PCG iterations (0: K solves of gm_tet_step, 1 / 2: K_T solves of
+    // the fault step in FP64 / FP32) and the stream they are captured on
+    cudaGraphExec_t pcg_graph[3] = {nullptr, nullptr, nullptr};
+    cudaStream_t cap_stream = nullptr;
+    bool use_graphs = true;
+    void drop_graphs()
+    {
+        for (auto& g : pcg_graph)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    }
+    ~gm_tet()
+    {
+        drop_graphs();
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
     int set_err(int code, const std::string& m) { err = m; return code; }
 };
 
@@ -291,15 +316,16 @@ namespace {
 
 template <typename T, int MODE>
 void launch(gm_tet* t, const TetCoef<T>& c, const T* xu, const T* xp, T* yu, T* yp, cudaStream_t s, const T* G,
-            const T* V)
+            const T* V, const int* skip)
 {
     const int N = (int)t->N;
     gm_tet_apply_kernel<T, MODE><<<(N + 127) / 128, 128, 0, s>>>(N, t->rowptr.as<int>(), t->adj.as<int>(),
-                                                                t->tets.as<int>(), G, V, c, xu, xp, yu, yp);
+                                                                t->tets.as<int>(), G, V, c, xu, xp, yu, yp, skip);
 }
 
+// skip: if non-null, the kernel does nothing while *skip != 0
 template <typename T>
-int apply_t(gm_tet* t, int which, const void* x, void* y, double dt, cudaStream_t s)
+int apply_t(gm_tet* t, int which, const void* x, void* y, double dt, cudaStream_t s, const int* skip = nullptr)
 {
     const long long N = t->N;
     TetCoef<T> c;
@@ -316,13 +342,13 @@ int apply_t(gm_tet* t, int which, const void* x, void* y, double dt, cudaStream_
     T* yu = static_cast<T*>(y);
     switch (which) {
     case GM_OP_KB:
-    case GM_OP_KT: launch<T, TM_K>(t, c, xu, nullptr, yu, nullptr, s, G, V); break;
-    case GM_OP_APU: launch<T, TM_APU>(t, c, nullptr, xu, yu, nullptr, s, G, V); break;
-    case GM_OP_AUP: launch<T, TM_AUP>(t, c, xu, nullptr, nullptr, yu, s, G, V); break;
-    case GM_OP_A22: launch<T, TM_S | TM_C>(t, c, nullptr, xu, nullptr, yu, s, G, V); break;
+    case GM_OP_KT: launch<T, TM_K>(t, c, xu, nullptr, yu, nullptr, s, G, V, skip); break;
+    case GM_OP_APU: launch<T, TM_APU>(t, c, nullptr, xu, yu, nullptr, s, G, V, skip); break;
+    case GM_OP_AUP: launch<T, TM_AUP>(t, c, xu, nullptr, nullptr, yu, s, G, V, skip); break;
+    case GM_OP_A22: launch<T, TM_S | TM_C>(t, c, nullptr, xu, nullptr, yu, s, G, V, skip); break;
     case GM_OP_J:
         c.cApu = T(-1);
-        launch<T, TM_K | TM_APU | TM_AUP | TM_S | TM_C>(t, c, xu, xu + 3 * N, yu, yu + 3 * N, s, G, V);
+        launch<T, TM_K | TM_APU | TM_AUP | TM_S | TM_C>(t, c, xu, xu + 3 * N, yu, yu + 3 * N, s, G, V, skip);
         break;
     default: return t->set_err(GM_EINVAL, "tet apply: unknown operator");
     }
@@ -364,15 +390,6 @@ __global__ void tet_zero_masked(int N, const uint8_t* mask, double* u, double* p
         for (int c = 0; c < 3; ++c)
             if ((m >> c) & 1u) u[c * N + n] = 0.0;
     if (p && ((m >> 3) & 1u)) p[n] = 0.0;
-}
-
-__global__ void tet_bjac(int N, const double* Kinv, const double* r, double* z)
-{
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    const double r0 = r[n], r1 = r[N + n], r2 = r[2 * N + n];
-    for (int i = 0; i < 3; ++i)
-        z[i * N + n] = Kinv[(3 * i) * N + n] * r0 + Kinv[(3 * i + 1) * N + n] * r1 + Kinv[(3 * i + 2) * N + n] * r2;
 }
 
 __global__ void tet_jac_p(int N, const double* Sd, const double* Cd, double dt, const uint8_t* mask, const double* r,
@@ -435,39 +452,31 @@ struct Stepper {
     void axpy(long long n, double a, const double* x, double* y) { tet_axpy<<<TET_RED_BLOCKS, 256, 0, s>>>(n, a, x, y); }
     void xpby(long long n, const double* x, double b, double* y) { tet_xpby<<<TET_RED_BLOCKS, 256, 0, s>>>(n, x, b, y); }
 
-    // x = K^-1 b (x from 0), block-Jacobi PCG to ||r|| <= rtol ||b||
+    // x = K^-1 b (x from 0), PCG with 3x3 nodal block Jacobi to ||r|| <= rtol ||b||,
+    // device-resident (scratch 0-3 and 14)
     int solve_k(const double* b, double* x, double rtol, int maxit, long long* its) {
-        const long long n = 3LL * N;
-        double *r = t->w[0].as<double>(), *z = t->w[1].as<double>(), *p = t->w[2].as<double>(), *q = t->w[3].as<double>();
-        cudaMemsetAsync(x, 0, n * 8, s);
-        cudaMemcpyAsync(r, b, n * 8, cudaMemcpyDeviceToDevice, s);
-        const double rr0 = dot(n, r, r);
-        if (rr0 == 0.0) return GM_OK;
-        tet_bjac<<<blocks(), 128, 0, s>>>(N, t->Kinv.as<double>(), r, z);
-        cudaMemcpyAsync(p, z, n * 8, cudaMemcpyDeviceToDevice, s);
-        double rz = dot(n, r, z);
-        for (int it = 1; it <= maxit; ++it) {
-            int rc = apply(GM_OP_KB, p, q, 0.0);
-            if (rc) return rc;
-            const double pq = dot(n, p, q);
-            if (!(pq > 0.0) || !std::isfinite(pq)) return t->set_err(GM_ENAN, "tet step: K not positive on a direction");
-            const double a = rz / pq;
-            axpy(n, a, p, x);
-            axpy(n, -a, q, r);
-            ++*its;
-            if (dot(n, r, r) <= rtol * rtol * rr0) return GM_OK;
-            tet_bjac<<<blocks(), 128, 0, s>>>(N, t->Kinv.as<double>(), r, z);
-            const double rzn = dot(n, r, z);
-            xpby(n, z, rzn / rz, p);
-            rz = rzn;
-        }
-        return t->set_err(GM_ENOCONV, "tet step: K solve did not converge");
+        TetPcg<double> e{N, s, t->w[14].as<double>(), t->w[0].as<double>(), t->w[1].as<double>(),
+                         t->w[2].as<double>(), t->w[3].as<double>(), t->pcg_st.as<TetPcgState>(),
+                         t->pcg_part.as<double>(),
+                         TetPrecT<double>{N, 0, t->Kinv.as<double>(), nullptr, nullptr, nullptr, nullptr},
+                         t->mask.as<uint8_t>()};
+        const int rc = e.solve(
+            b, x, rtol, maxit, its,
+            [&](const double* p, double* q, const int* skip, cudaStream_t cs) {
+                apply_t<double>(t, GM_OP_KB, p, q, 0.0, cs, skip);
+            },
+            t->use_graphs ? &t->pcg_graph[0] : nullptr, &t->cap_stream);
+        if (rc == 2) return t->set_err(GM_ENAN, "tet step: K not positive on a direction");
+        if (rc == 3) return t->set_err(GM_ENOCONV, "tet step: K solve did not converge");
+        if (rc < 0) return t->set_err(GM_ECUDA, std::string("tet step: ") + cudaGetErrorString(cudaGetLastError()));
+        return GM_OK;
     }
 };
 
 // nodal 3x3 blocks of K and the diagonals of S and C (host), uploaded
 int tet_prepare(gm_tet* t)
 {
+    t->drop_graphs();   // the vectors they hold are reallocated below
     const long long N = t->N, M = t->M;
     const double lam = t->E * t->nu / ((1 + t->nu) * (1 - 2 * t->nu)), mu = t->E / (2 * (1 + t->nu));
     std::vector<double> B(9 * N, 0.0), Sd(N, 0.0), Cd(N, 0.0);
@@ -514,7 +523,9 @@ int tet_prepare(gm_tet* t)
     cudaError_t ce;
     if ((ce = t->Kinv.put(Kinv.data(), Kinv.size() * 8)) != cudaSuccess || (ce = t->Sd.put(Sd.data(), N * 8)) != cudaSuccess ||
         (ce = t->Cd.put(Cd.data(), N * 8)) != cudaSuccess || (ce = t->mask.put(mk.data(), N)) != cudaSuccess ||
-        (ce = t->dfu.put(fu.data(), 3 * N * 8)) != cudaSuccess || (ce = t->part.alloc(TET_RED_BLOCKS * 8)) != cudaSuccess)
+        (ce = t->dfu.put(fu.data(), 3 * N * 8)) != cudaSuccess || (ce = t->part.alloc(TET_RED_BLOCKS * 8)) != cudaSuccess ||
+        (ce = t->pcg_st.alloc(sizeof(TetPcgState))) != cudaSuccess ||
+        (ce = t->pcg_part.alloc(2 * TPCG_BLOCKS * sizeof(double))) != cudaSuccess)
         return t->set_err(GM_ECUDA, std::string("tet step: ") + cudaGetErrorString(ce));
     for (auto& b : t->w)
         if ((ce = b.alloc(3 * N * 8)) != cudaSuccess)
@@ -735,18 +746,20 @@ __global__ void tetf_return_map(PairGeo g, const double* u, const double* du, co
     }
 }
 
-// y(+) += A D [[x]],  y(-) -= A D [[x]]
-__global__ void tetf_pair_tangent(PairGeo g, const double* D, const double* x, double* y)
+// y(+) += A D [[x]],  y(-) -= A D [[x]]  (nothing while *skip != 0)
+template <typename T>
+__global__ void tetf_pair_tangent(PairGeo g, const T* D, const T* x, T* y, const int* skip)
 {
+    if (skip != nullptr && *skip != 0) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.P) return;
     const int P = g.P, N = g.N, a = g.pm[i], b = g.pp[i];
-    double j[3];
+    T j[3];
     for (int c = 0; c < 3; ++c) j[c] = x[c * N + b] - x[c * N + a];
-    const double d0 = D[i], d1 = D[P + i], d2 = D[2 * P + i], d3 = D[3 * P + i], d4 = D[4 * P + i], d5 = D[5 * P + i];
-    const double A = g.area[i];
-    const double v[3] = {A * (d0 * j[0] + d1 * j[1] + d2 * j[2]), A * (d1 * j[0] + d3 * j[1] + d4 * j[2]),
-                         A * (d2 * j[0] + d4 * j[1] + d5 * j[2])};
+    const T d0 = D[i], d1 = D[P + i], d2 = D[2 * P + i], d3 = D[3 * P + i], d4 = D[4 * P + i], d5 = D[5 * P + i];
+    const T A = (T)g.area[i];
+    const T v[3] = {A * (d0 * j[0] + d1 * j[1] + d2 * j[2]), A * (d1 * j[0] + d3 * j[1] + d4 * j[2]),
+                    A * (d2 * j[0] + d4 * j[1] + d5 * j[2])};
     for (int c = 0; c < 3; ++c) {
         y[c * N + b] += v[c];
         y[c * N + a] -= v[c];
@@ -906,6 +919,7 @@ __global__ void __launch_bounds__(256) tetf_wdot(long long n, const double* x, c
 // when tied), masks, scaled-norm weights, loads, in-situ floor; uploads
 int tetf_prepare(gm_tet* t)
 {
+    t->drop_graphs();   // the vectors they hold are reallocated below
     const long long N = t->N, M = t->M, P = t->P;
     const double lam = t->E * t->nu / ((1 + t->nu) * (1 - 2 * t->nu)), mu = t->E / (2 * (1 + t->nu));
     const double cond = t->k / t->mu_f;
@@ -996,10 +1010,17 @@ int tetf_prepare(gm_tet* t)
         (ce = t->f_dKm.put(dKm.data(), 3 * N * 8)) != cudaSuccess ||
         (ce = t->f_invdK.put(invdK.data(), 3 * N * 8)) != cudaSuccess || (ce = t->f_dAm.alloc(N * 8)) != cudaSuccess ||
         (ce = t->f_invdA.alloc(N * 8)) != cudaSuccess || (ce = t->f_mask.put(mk.data(), N)) != cudaSuccess ||
-        (ce = t->f_err.alloc(sizeof(int))) != cudaSuccess || (ce = t->part.alloc(TET_RED_BLOCKS * 8)) != cudaSuccess)
+        (ce = t->f_err.alloc(sizeof(int))) != cudaSuccess || (ce = t->part.alloc(TET_RED_BLOCKS * 8)) != cudaSuccess ||
+        (ce = t->f_Pinv.alloc(36 * P * 8)) != cudaSuccess || (ce = t->f_Pinv32.alloc(36 * P * 4)) != cudaSuccess ||
+        (ce = t->f_Kinv32.alloc(9 * N * 4)) != cudaSuccess || (ce = t->f_D32.alloc(6 * P * 4)) != cudaSuccess ||
+        (ce = t->pcg_st.alloc(sizeof(TetPcgState))) != cudaSuccess ||
+        (ce = t->pcg_part.alloc(2 * TPCG_BLOCKS * sizeof(double))) != cudaSuccess)
         return t->set_err(GM_ECUDA, std::string("tet fault: ") + cudaGetErrorString(ce));
     for (auto& b : t->fw)
         if ((ce = b.alloc(3 * N * 8)) != cudaSuccess)
+            return t->set_err(GM_ECUDA, std::string("tet fault: ") + cudaGetErrorString(ce));
+    for (auto& b : t->fw32)
+        if ((ce = b.alloc(3 * N * 4)) != cudaSuccess)
             return t->set_err(GM_ECUDA, std::string("tet fault: ") + cudaGetErrorString(ce));
     t->fault_ready = true;
     return GM_OK;
@@ -1009,6 +1030,7 @@ struct FStepper {
     gm_tet* t;
     cudaStream_t s;
     int N, P;
+    bool f32 = false;          // inner K_T solves in FP32
     long long applies = 0;
 
     PairGeo geo() const
@@ -1054,8 +1076,16 @@ struct FStepper {
     {
         int rc = bulk(GM_OP_KB, x, y, 0.0);
         if (rc) return rc;
-        tetf_pair_tangent<<<pb(), 128, 0, s>>>(geo(), t->f_D.as<double>(), x, y);
+        tetf_pair_tangent<double><<<pb(), 128, 0, s>>>(geo(), t->f_D.as<double>(), x, y, nullptr);
         return GM_OK;
+    }
+    // q = K_T p in the inner-solve precision, unmasked (the PCG masks it)
+    template <typename T>
+    void KT_inner(const T* p, T* q, const int* skip, cudaStream_t cs)
+    {
+        apply_t<T>(t, GM_OP_KB, p, q, 0.0, cs, skip);
+        const T* D = sizeof(T) == 8 ? (const T*)t->f_D.p : (const T*)t->f_D32.p;
+        tetf_pair_tangent<T><<<pb(), 128, 0, cs>>>(geo(), D, p, q, skip);
     }
     int APU_raw(const double* xp, double* yu)
     {
@@ -1092,34 +1122,42 @@ struct FStepper {
     int AUP(const double* x, double* y) { int rc = AUP_raw(x, y); if (!rc) mask_p(y); return rc; }
     int A22(const double* x, double* y, double dt) { int rc = A22_raw(x, y, dt); if (!rc) mask_p(y); return rc; }
 
-    // x = K_T^-1 b from x = 0, block-Jacobi PCG to ||r|| <= rtol ||b||  (scratch 1-4)
+    // x = K_T^-1 b from x = 0 to ||r|| <= rtol ||b||: device-resident PCG with
+    // nodal 3x3 and lip-pair 6x6 block Jacobi, in FP32 (operator, blocks and
+    // vectors) when f32 is set  (scratch 1-4 and 24, or the FP32 scratch)
     int solve_kt(const double* b, double* x, double rtol, int maxit, long long* its)
     {
-        const long long n = 3LL * N;
-        double *r = w(1), *z = w(2), *p = w(3), *q = w(4);
-        cudaMemsetAsync(x, 0, n * 8, s);
-        copy(r, b, n);
-        const double rr0 = dot(n, r, r);
-        if (rr0 == 0.0) return GM_OK;
-        tet_bjac<<<nb(), 128, 0, s>>>(N, t->f_Kinv.as<double>(), r, z);
-        copy(p, z, n);
-        double rz = dot(n, r, z);
-        for (int it = 1; it <= maxit; ++it) {
-            int rc = KT(p, q);
-            if (rc) return rc;
-            const double pq = dot(n, p, q);
-            if (!(pq > 0.0) || !std::isfinite(pq)) return t->set_err(GM_ENAN, "tet fault: K_T not positive on a direction");
-            const double a = rz / pq;
-            axpy(n, a, p, x);
-            axpy(n, -a, q, r);
-            ++*its;
-            if (dot(n, r, r) <= rtol * rtol * rr0) return GM_OK;
-            tet_bjac<<<nb(), 128, 0, s>>>(N, t->f_Kinv.as<double>(), r, z);
-            const double rzn = dot(n, r, z);
-            xpby(n, z, rzn / rz, p);
-            rz = rzn;
+        int rc;
+        const long long its0 = *its;
+        TetPcgState* ps = t->pcg_st.as<TetPcgState>();
+        double* part = t->pcg_part.as<double>();
+        const uint8_t* mk = t->f_mask.as<uint8_t>();
+        if (f32) {
+            float* v[5];
+            for (int k = 0; k < 5; ++k) v[k] = t->fw32[k].as<float>();
+            TetPcg<float> e{N, s, v[0], v[1], v[2], v[3], v[4], ps, part,
+                            TetPrecT<float>{N, P, t->f_Kinv32.as<float>(), t->f_n2p.as<int>(), t->f_pm.as<int>(),
+                                            t->f_pp.as<int>(), t->f_Pinv32.as<float>()},
+                            mk};
+            rc = e.solve(
+                b, x, rtol, maxit, its,
+                [&](const float* p, float* q, const int* skip, cudaStream_t cs) { KT_inner<float>(p, q, skip, cs); },
+                t->use_graphs ? &t->pcg_graph[2] : nullptr, &t->cap_stream);
+        } else {
+            TetPcg<double> e{N, s, w(24), w(1), w(2), w(3), w(4), ps, part,
+                             TetPrecT<double>{N, P, t->f_Kinv.as<double>(), t->f_n2p.as<int>(), t->f_pm.as<int>(),
+                                              t->f_pp.as<int>(), t->f_Pinv.as<double>()},
+                             mk};
+            rc = e.solve(
+                b, x, rtol, maxit, its,
+                [&](const double* p, double* q, const int* skip, cudaStream_t cs) { KT_inner<double>(p, q, skip, cs); },
+                t->use_graphs ? &t->pcg_graph[1] : nullptr, &t->cap_stream);
         }
-        return t->set_err(GM_ENOCONV, "tet fault: K_T solve did not converge");
+        applies += *its - its0;
+        if (rc == 2) return t->set_err(GM_ENAN, "tet fault: K_T not positive on a direction");
+        if (rc == 3) return t->set_err(GM_ENOCONV, "tet fault: K_T solve did not converge");
+        if (rc < 0) return t->set_err(GM_ECUDA, std::string("tet fault: ") + cudaGetErrorString(cudaGetLastError()));
+        return GM_OK;
     }
 
     // [K_T, -A_pu; A_up, S + dt C] [x1; x2] = [b1; b2] by Prevost's partitioned
@@ -1402,7 +1440,8 @@ extern "C" int gm_tet_fault_step(gm_tet* t, double dt, double* u, double* p, con
     if (!t) return GM_EINVAL;
     if (!t->has_mesh || !t->has_mat || !t->has_fault) return t->set_err(GM_ESTATE, "tet fault step: mesh, materials and fault required");
     if (!u || !p || !opts || !(dt > 0) || !(opts->newton_rtol > 0) || opts->newton_maxit < 1 || !(opts->outer_rtol > 0) ||
-        opts->outer_maxit < 1 || !(opts->inner_rtol > 0) || opts->inner_maxit < 1)
+        opts->outer_maxit < 1 || !(opts->inner_rtol > 0) || opts->inner_maxit < 1 ||
+        (opts->precision != GM_F64 && opts->precision != GM_F32))
         return t->set_err(GM_EINVAL, "tet fault step: bad arguments");
     cudaSetDevice(t->device);
     int rc;
@@ -1411,6 +1450,7 @@ extern "C" int gm_tet_fault_step(gm_tet* t, double dt, double* u, double* p, con
     const int N = (int)t->N, P = (int)t->P;
     const long long n3 = 3LL * N;
     FStepper st{t, s, N, P};
+    st.f32 = opts->precision == GM_F32;
     const gm_fault_params& fp = t->fpar;
     double *du = st.w(13), *dp = st.w(14), *b1 = st.w(15), *b2 = st.w(16), *x1 = st.w(19), *x2 = st.w(20);
     double* pst = st.w(23);
@@ -1449,10 +1489,18 @@ extern "C" int gm_tet_fault_step(gm_tet* t, double dt, double* u, double* p, con
         tetf_bjac_build<<<st.nb(), 128, 0, s>>>(N, P, t->f_Kblk.as<double>(), t->f_n2p.as<int>(), t->f_area.as<double>(),
                                                t->f_D.as<double>(), t->f_mask.as<uint8_t>(), t->f_Kinv.as<double>(),
                                                t->f_err.as<int>());
+        tpcg_pair_inverse<<<st.pb(), 128, 0, s>>>(N, P, t->f_Kblk.as<double>(), t->f_pm.as<int>(), t->f_pp.as<int>(),
+                                                  t->f_area.as<double>(), t->f_D.as<double>(), t->f_mask.as<uint8_t>(),
+                                                  t->f_Pinv.as<double>(), t->f_err.as<int>());
+        if (st.f32) {
+            tpcg_cast<float><<<TPCG_BLOCKS, TPCG_NT, 0, s>>>(9LL * N, t->f_Kinv.as<double>(), t->f_Kinv32.as<float>());
+            tpcg_cast<float><<<TPCG_BLOCKS, TPCG_NT, 0, s>>>(36LL * P, t->f_Pinv.as<double>(), t->f_Pinv32.as<float>());
+            tpcg_cast<float><<<TPCG_BLOCKS, TPCG_NT, 0, s>>>(6LL * P, t->f_D.as<double>(), t->f_D32.as<float>());
+        }
         int herr = 0;
         cudaMemcpyAsync(&herr, t->f_err.p, sizeof(int), cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
-        if (herr) return t->set_err(GM_ENAN, "tet fault step: singular nodal block of K_T");
+        if (herr) return t->set_err(GM_ENAN, "tet fault step: singular nodal or lip-pair block of K_T");
         if ((rc = st.prevost(b1, b2, x1, x2, dt, *opts, &outer, &inner))) return rc;
         st.axpy(n3, 1.0, x1, du);
         st.axpy(N, 1.0, x2, dp);

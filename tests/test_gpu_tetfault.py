@@ -47,8 +47,12 @@ STEP_CASES = {
 }
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32_refined"])
 @pytest.mark.parametrize("case", sorted(STEP_CASES))
-def test_fault_steps_match_oracle(case):
+def test_fault_steps_match_oracle(case, precision):
+    """FP64, and FP32-refined (FP32 inner K_T solves inside the FP64 Newton
+    loop, which refines them to the same Newton tolerance): the oracle's
+    steps within 1e-9 and its fault states."""
     need_gpu()
     import paper_2410_17133_gb300 as gm
     make, nsteps = STEP_CASES[case]
@@ -58,7 +62,8 @@ def test_fault_steps_match_oracle(case):
     u = torch.zeros((3, s.N), dtype=torch.float64, device="cuda")
     p = torch.zeros(s.N, dtype=torch.float64, device="cuda")
     for k, dt in enumerate(prob.dts[:nsteps]):
-        rep = s.fault_step(dt, u, p)
+        rep = s.fault_step(dt, u, p, precision=precision)
+        print(case, precision, k, rep["newton"], rep["outer"], rep["inner_k"])
         st = s.fault_state()
         o = res[k]
         assert np.array_equal(st["flags"], o.flags), f"step {k}"
