@@ -42,11 +42,14 @@ __global__ void __launch_bounds__(128) gm_tet_apply_kernel(int N, const int* row
     constexpr bool IN_P = (MODE & (TM_APU | TM_S | TM_C)) != 0;
     constexpr bool OUT_U = (MODE & (TM_K | TM_APU)) != 0;
     constexpr bool OUT_P = (MODE & (TM_AUP | TM_S | TM_C)) != 0;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+    // one warp per node: lane l takes the node's incident elements l, l + 32, ...
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= N) return;                     // uniform over the warp
+    const int n = (int)wid;
     T au[3] = {T(0), T(0), T(0)};
     T ap = T(0);
-    for (int q = rowptr[n]; q < rowptr[n + 1]; ++q) {
+    for (int q = rowptr[n] + lane; q < rowptr[n + 1]; q += 32) {
         const int code = adj[q];
         const int e = code >> 2, a = code & 3;
         int v[4];
@@ -104,6 +107,16 @@ __global__ void __launch_bounds__(128) gm_tet_apply_kernel(int N, const int* row
         if constexpr ((MODE & TM_S) != 0) ap += c.cS * c.invM * vol * T(0.05) * (psum + pa);
         if constexpr ((MODE & TM_C) != 0) ap += c.cC * c.cond * vol * (gax * gp[0] + gay * gp[1] + gaz * gp[2]);
     }
+    // fixed butterfly over the lanes: the same sums in the same order every call
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        if constexpr (OUT_U) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) au[c] += __shfl_xor_sync(0xffffffffu, au[c], o);
+        }
+        if constexpr (OUT_P) ap += __shfl_xor_sync(0xffffffffu, ap, o);
+    }
+    if (lane != 0) return;
     if constexpr (OUT_U) {
         yu[n] = au[0];
         yu[N + n] = au[1];
@@ -319,8 +332,9 @@ void launch(gm_tet* t, const TetCoef<T>& c, const T* xu, const T* xp, T* yu, T* 
             const T* V, const int* skip)
 {
     const int N = (int)t->N;
-    gm_tet_apply_kernel<T, MODE><<<(N + 127) / 128, 128, 0, s>>>(N, t->rowptr.as<int>(), t->adj.as<int>(),
-                                                                t->tets.as<int>(), G, V, c, xu, xp, yu, yp, skip);
+    const unsigned blocks = (unsigned)((32LL * N + 127) / 128);   // one warp per node
+    gm_tet_apply_kernel<T, MODE><<<blocks, 128, 0, s>>>(N, t->rowptr.as<int>(), t->adj.as<int>(), t->tets.as<int>(), G,
+                                                        V, c, xu, xp, yu, yp, skip);
 }
 
 // skip: if non-null, the kernel does nothing while *skip != 0

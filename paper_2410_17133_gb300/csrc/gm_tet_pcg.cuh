@@ -35,47 +35,57 @@ struct TetPrecT {
     const T* Pinv;      // 36P, (6 r + c) * P + i; constrained rows / columns 0
 };
 
-// Block sum of (a, b); the last block to finish gets the grid sums in (A, B)
-// (thread 0 only) and returns true there.
-__device__ inline bool tpcg_reduce2(double a, double b, double* part, unsigned* ticket, double& A, double& B)
+// Block sum of (a, b) in a fixed tree (warp butterfly, then the warps in order)
+__device__ inline void tpcg_block_sum2(double& a, double& b)
 {
     __shared__ double sa[TPCG_NT / 32], sb[TPCG_NT / 32];
-    __shared__ bool last;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
     }
+    __syncthreads();                       // the shared words may still be read by a previous call
     if ((threadIdx.x & 31) == 0) {
         sa[threadIdx.x >> 5] = a;
         sb[threadIdx.x >> 5] = b;
     }
     __syncthreads();
+    a = 0.0;
+    b = 0.0;
+    for (int w = 0; w < TPCG_NT / 32; ++w) {
+        a += sa[w];
+        b += sb[w];
+    }
+}
+
+// Grid sum of (a, b): each block writes its partials; the last block to finish
+// (ticket counter) sums all partials, thread t taking blocks t, t + 256, ...,
+// then the block tree, so the order is fixed.  Returns true on thread 0 of the
+// last block, which holds the sums in (A, B).
+__device__ inline bool tpcg_reduce2(double a, double b, double* part, unsigned* ticket, double& A, double& B)
+{
+    __shared__ bool last;
+    tpcg_block_sum2(a, b);
     if (threadIdx.x == 0) {
-        double ta = 0.0, tb = 0.0;
-        for (int w = 0; w < TPCG_NT / 32; ++w) {
-            ta += sa[w];
-            tb += sb[w];
-        }
-        part[2 * blockIdx.x] = ta;
-        part[2 * blockIdx.x + 1] = tb;
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
         __threadfence();
-        const unsigned tk = atomicAdd(ticket, 1u);
-        last = tk == gridDim.x - 1;
-        if (last) {
-            __threadfence();
-            const volatile double* vp = part;
-            A = 0.0;
-            B = 0.0;
-            for (unsigned k = 0; k < gridDim.x; ++k) {
-                A += vp[2 * k];
-                B += vp[2 * k + 1];
-            }
-            *ticket = 0u;
-        }
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    return threadIdx.x == 0 && last;
+    if (!last) return false;
+    __threadfence();
+    double pa = 0.0, pb = 0.0;
+    for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
+        pa += __ldcg(part + 2 * k);
+        pb += __ldcg(part + 2 * k + 1);
+    }
+    tpcg_block_sum2(pa, pb);
+    if (threadIdx.x != 0) return false;
+    A = pa;
+    B = pb;
+    *ticket = 0u;
+    return true;
 }
 
 // r = b (cast to T), x = 0; state reset

@@ -1,6 +1,6 @@
 """Sec. 5's stress-rotation study on the faulted aquifer at half size
 (64 x 128 x 128 hexes, 1.09 M nodes): for each rotation beta of the horizontal
-principal stresses about the vertical, FP32-refined steps of 6 h from the
+principal stresses about the vertical, FP32-refined steps from the
 in-situ state until the first fault pair slips (run_until_slip), and the
 injected volume Q t at that onset.  Only the angles whose printed stress
 gradients leave the fault below failure before injection are run (outside
@@ -8,8 +8,9 @@ gradients leave the fault below failure before injection are run (outside
 fault most stable with the larger horizontal stress across it (beta = 90); the
 volume to the onset must therefore grow from beta = 60 to 90 and fall again to
 120, and beta and 180 - beta (the same Coulomb ratio) must agree within the
-step size.  About 10 minutes on a GB300, so it runs only when
-GM_ROTATION_SWEEP=1; the table of the last run is recorded with the results."""
+step size.  Steps of one day, up to 400 days of injection.  About 10
+minutes on a GB300, so it runs only when GM_ROTATION_SWEEP=1; the table of the
+last run is recorded with the results."""
 import os
 
 import numpy as np
@@ -28,7 +29,7 @@ BETAS = [0.0, 60.0, 75.0, 90.0, 105.0, 120.0, 180.0]
 def test_injected_volume_to_slip_onset_against_beta():
     need_gpu()
     import paper_2410_17133_gb300 as gm
-    dt, nmax = 6 * 3600.0, 200
+    dt, nmax = 86400.0, 400
     vol = {}
     for beta in BETAS:
         prob = W.faulted_aquifer(64, 128, 128, steps=nmax, dt=dt, beta_deg=beta)
