@@ -13,9 +13,9 @@
 //   - prolongation is trilinear interpolation inside each block, restriction
 //     its transpose (full weighting), so the cycle never couples the lips;
 //   - smoothing is a degree-2 Chebyshev polynomial in M^-1 K_T with M the
-//     nodal / lip-pair block Jacobi, over [0.25, 1.15] x the largest
+//     nodal / lip-pair block Jacobi, over [0.15, 1.15] x the largest
 //     eigenvalue (power iteration at set-up); the coarsest level runs a
-//     degree-16 polynomial (by default) over [0.01, 1.15] x that eigenvalue.
+//     degree-24 polynomial (by default) over [0.003, 1.15] x that eigenvalue.
 // Pre- and post-smoothing use the same polynomial, so the cycle is a
 // symmetric positive definite operator and plain PCG stays valid.
 // Everything is enqueued on the caller's stream without host synchronisation
@@ -34,12 +34,12 @@ constexpr int MG_MAX_COARSE_DEG = 32;
 // tuning (environment, read at set-up): coarse grids below the first keep at
 // least GM_MG_MIN_CELLS cells per direction (default 10; the first coarse
 // grid only needs 2); the coarsest level runs a Chebyshev polynomial of degree
-// GM_MG_COARSE_DEG (default 16).  Measured on the 160^3 inclined workload
-// (FP32-refined): stopping at 10^3 instead of 5^3 and degree 16 instead of 8
-// cut the K_T iterations from about 400 to 330 per step and the step from
-// 0.81 s to 0.71 s; the 64^3 slip-front step is unchanged.
+// GM_MG_COARSE_DEG (default 24).  Measured on the 160^3 inclined workload
+// (FP32-refined), with the interval ends below: stopping at 10^3 instead of
+// 5^3 and a degree-24 coarsest polynomial take the step from 0.81 s to 0.55 s
+// (K_T iterations per step about 400 -> 220).
 constexpr int MG_MIN_CELLS = 10;
-constexpr int MG_COARSE_DEG = 16;
+constexpr int MG_COARSE_DEG = 24;
 int mg_min_cells()
 {
     const char* v = std::getenv("GM_MG_MIN_CELLS");
@@ -54,8 +54,8 @@ int mg_smooth_deg()
     return (n >= 1 && n <= MG_MAX_COARSE_DEG) ? n : MG_SMOOTH_DEG;
 }
 // lower ends of the Chebyshev intervals as fractions of the largest
-// eigenvalue: GM_MG_SMOOTH_LO (smoothing, default 0.25) and GM_MG_COARSE_LO
-// (coarsest level, default 0.0115 = 0.01 x 1.15)
+// eigenvalue: GM_MG_SMOOTH_LO (smoothing, default 0.15) and GM_MG_COARSE_LO
+// (coarsest level, default 0.003)
 double mg_frac(const char* name, double dflt)
 {
     const char* v = std::getenv(name);
@@ -619,7 +619,7 @@ int build(gm_ctx* c)
         L.deg = last ? mg_coarse_deg() : mg_smooth_deg();
         L.coef_off = off;
         const double hi = 1.15 * L.lmax;
-        const double lo = (last ? mg_frac("GM_MG_COARSE_LO", 0.0115) : mg_frac("GM_MG_SMOOTH_LO", 0.25)) * L.lmax;
+        const double lo = (last ? mg_frac("GM_MG_COARSE_LO", 0.003) : mg_frac("GM_MG_SMOOTH_LO", 0.15)) * L.lmax;
         cheb_coefs(lo, hi, L.deg, coef);
         off += L.deg;
     }
