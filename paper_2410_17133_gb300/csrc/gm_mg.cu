@@ -193,13 +193,18 @@ struct FaultK {
 // d = c1 d + c2 z (c1 = 0: d = c2 z), x = x + d (xzero: x = d).  With fk.D
 // set, y holds the bulk product only and the pair thread adds
 // +-A_i D [[x]] to the two lips first (the fault rows of K_T).
+// mode bits: CHEB_XZERO (x = 0 before the step), CHEB_D_FROM_X (the previous
+// d is x: the step after an x = 0 step, which then need not store d) and
+// CHEB_NO_D (the last step of a polynomial: d is not needed afterwards).
+enum : int { CHEB_XZERO = 1, CHEB_D_FROM_X = 2, CHEB_NO_D = 4 };
 template <typename T>
 __global__ void __launch_bounds__(256) mg_cheb_kernel(long long N, const T* b, const T* y, T* x, T* d,
-                                                      const T* mi, PairPrec<T> pp, const double* coef, int xzero,
+                                                      const T* mi, PairPrec<T> pp, const double* coef, int mode,
                                                       const int* skip, FaultK<T> fk)
 {
     if (skip && *skip) return;
     const T c1 = (T)coef[0], c2 = (T)coef[1];
+    const bool xzero = (mode & CHEB_XZERO) != 0, dfx = (mode & CHEB_D_FROM_X) != 0, keepd = (mode & CHEB_NO_D) == 0;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
         const long long dd = n - pp.lo;
@@ -245,9 +250,10 @@ __global__ void __launch_bounds__(256) mg_cheb_kernel(long long N, const T* b, c
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     const long long k = c * N + nd[s];
-                    const T dn = c1 == T(0) ? c2 * z6[3 * s + c] : fma(c1, d[k], c2 * z6[3 * s + c]);
-                    d[k] = dn;
-                    x[k] = xzero ? dn : x[k] + dn;
+                    const T xv = xzero ? T(0) : x[k];
+                    const T dn = c1 == T(0) ? c2 * z6[3 * s + c] : fma(c1, dfx ? xv : d[k], c2 * z6[3 * s + c]);
+                    if (keepd) d[k] = dn;
+                    x[k] = xv + dn;
                 }
             continue;
         }
@@ -258,9 +264,10 @@ __global__ void __launch_bounds__(256) mg_cheb_kernel(long long N, const T* b, c
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const long long k = c * N + n;
-            const T dn = c1 == T(0) ? c2 * z[c] : fma(c1, d[k], c2 * z[c]);
-            d[k] = dn;
-            x[k] = xzero ? dn : x[k] + dn;
+            const T xv = xzero ? T(0) : x[k];
+            const T dn = c1 == T(0) ? c2 * z[c] : fma(c1, dfx ? xv : d[k], c2 * z[c]);
+            if (keepd) d[k] = dn;
+            x[k] = xv + dn;
         }
     }
 }
@@ -433,15 +440,16 @@ FaultK<T> level_fault(gm_ctx* x)
 }
 
 template <typename T>
-int cheb_step(gm_ctx* c, const MGLevel& L, int k, bool xzero, bool fused, const int* skip, cudaStream_t s)
+int cheb_step(gm_ctx* c, const MGLevel& L, int k, int mode, bool fused, const int* skip, cudaStream_t s)
 {
     gm_ctx* x = L.cx;
     const LV<T> v = lv<T>(L);
     const double* cf = c->mg_coef.as<double>() + 2 * (L.coef_off + k);
     FaultK<T> fk = level_fault<T>(x);
     if (!fused) fk.D = nullptr;
+    const bool xzero = (mode & CHEB_XZERO) != 0;
     mg_cheb_kernel<T><<<mg_blocks(x->N), 256, 0, s>>>(x->N, v.b, xzero ? nullptr : v.y, v.x, v.d, level_inv<T>(x),
-                                                    level_pairs<T>(x), cf, xzero ? 1 : 0, skip, fk);
+                                                    level_pairs<T>(x), cf, mode, skip, fk);
     GM_LAUNCHED(c);
     return GM_OK;
 }
@@ -460,7 +468,10 @@ int smooth(gm_ctx* c, const MGLevel& L, int deg, bool xzero, const int* skip, cu
             rc = fused ? apply_kb(L.cx, v.x, v.y, skip, s) : apply_kt(L.cx, v.x, v.y, skip, s);
             if (rc) return rc;
         }
-        if ((rc = cheb_step<T>(c, L, k, z0, fused, skip, s))) return rc;
+        // after an x = 0 step d equals x; the last step's d is never read
+        const int mode = (z0 ? CHEB_XZERO : 0) | (xzero && k == 1 ? CHEB_D_FROM_X : 0) |
+                         (z0 || k == deg - 1 ? CHEB_NO_D : 0);
+        if ((rc = cheb_step<T>(c, L, k, mode, fused, skip, s))) return rc;
     }
     return GM_OK;
 }
@@ -536,7 +547,8 @@ int estimate_lmax(gm_ctx* c, MGLevel& L)
         FaultK<float> nofk = level_fault<float>(x);
         nofk.D = nullptr;
         mg_cheb_kernel<float><<<GM_RED_BLOCKS, 256>>>(x->N, L.y, nullptr, L.x, L.d, x->dKinv32.as<float>(),
-                                                      level_pairs<float>(x), unit, 1, nullptr, nofk);
+                                                      level_pairs<float>(x), unit, CHEB_XZERO | CHEB_NO_D, nullptr,
+                                                      nofk);
         GM_LAUNCHED(c);
         double nw;
         if ((rc = norm2(c, n3, L.x, &nw))) return rc;
