@@ -383,6 +383,7 @@ struct BJArgs {
     double Aq;
     double* inv64;       // 6N
     float* inv32;        // 6N
+    __nv_bfloat16* inv16;   // 6N (the multigrid smoother's copy), or null
 };
 
 __global__ void __launch_bounds__(256) gm_block_jacobi_kernel(const BJArgs a)
@@ -424,6 +425,7 @@ __global__ void __launch_bounds__(256) gm_block_jacobi_kernel(const BJArgs a)
     for (int q = 0; q < 6; ++q) {
         a.inv64[q * N + n] = I[q];
         a.inv32[q * N + n] = (float)I[q];
+        if (a.inv16) a.inv16[q * N + n] = __float2bfloat16_rn((float)I[q]);
     }
 }
 
@@ -493,6 +495,7 @@ int gm_launch_block_jacobi(gm_ctx* c, cudaStream_t s)
     a.Aq = c->Aq;
     a.inv64 = c->dKinv64.as<double>();
     a.inv32 = c->dKinv32.as<float>();
+    a.inv16 = c->dKinv16.as<__nv_bfloat16>();
     const int nblk = (int)((c->N + 255) / 256);
     gm_block_jacobi_kernel<<<nblk, 256, 0, s>>>(a);
     GM_LAUNCHED(c);

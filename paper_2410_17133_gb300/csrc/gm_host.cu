@@ -907,7 +907,7 @@ int bind_impl(gm_ctx* c)
         {&c->dtauc, (size_t)4 * P * 8}, {&c->dfpair, (size_t)P * 8},
         {&c->dinsitu, (size_t)3 * P * 8},
         {&c->ddiagK, (size_t)N3 * 8}, {&c->ddiagA, (size_t)N * 8},
-        {&c->dKinv64, (size_t)12 * N * 8}, {&c->dKinv32, (size_t)6 * N * 4},
+        {&c->dKinv64, (size_t)12 * N * 8}, {&c->dKinv32, (size_t)6 * N * 4}, {&c->dKinv16, (size_t)6 * N * 2},
         {&c->dKpair64, (size_t)36 * std::max<long long>(P, 1) * 8}, {&c->dKpair32, (size_t)36 * std::max<long long>(P, 1) * 4},
         {&c->dAinv64, (size_t)N * 8}, {&c->dAinv32, (size_t)N * 4},
         {&c->dFS64, (size_t)nel * 8}, {&c->dFS32, (size_t)nel * 4},

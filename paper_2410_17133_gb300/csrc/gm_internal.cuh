@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libgm.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -425,6 +426,7 @@ struct gm_ctx {
     double adj_prtol = 1e-8;     // preconditioner tolerance
     int adj_schur = 0;           // preconditioner's Schur preconditioner
     DevBuf ddiagK, ddiagA, dKinv64, dKinv32, dAinv64, dAinv32;
+    DevBuf dKinv16;                                    // 6N bf16 copy of the nodal block inverses (multigrid smoother)
     DevBuf dKpair64, dKpair32;                         // 6x6 inverse blocks of the lip pairs (36 per pair)
     bool pair_prec = true;                             // K_T preconditioner: lip pairs as 6x6 blocks
     int precond = 1;                                   // FP32 K_T solves: 0 block Jacobi, 1 multigrid

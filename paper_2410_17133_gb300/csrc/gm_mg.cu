@@ -21,6 +21,7 @@
 // Everything is enqueued on the caller's stream without host synchronisation
 // (except the one-time set-up), so the PCG iterations remain graph-capturable.
 #include <cmath>
+#include <type_traits>
 #include <cstdlib>
 
 #include "gm_internal.cuh"
@@ -196,10 +197,19 @@ struct FaultK {
 // mode bits: CHEB_XZERO (x = 0 before the step), CHEB_D_FROM_X (the previous
 // d is x: the step after an x = 0 step, which then need not store d) and
 // CHEB_NO_D (the last step of a polynomial: d is not needed afterwards).
+// The nodal block inverses are read as MT: bf16 in the FP32 smoother (a
+// preconditioner only needs to be fixed and SPD; halving its bytes cuts the
+// smoothing step's traffic), T in the FP64 one.
 enum : int { CHEB_XZERO = 1, CHEB_D_FROM_X = 2, CHEB_NO_D = 4 };
-template <typename T>
+template <typename T, typename MT>
+__device__ inline T mg_ld(const MT* p)
+{
+    if constexpr (std::is_same<MT, __nv_bfloat16>::value) return (T)__bfloat162float(*p);
+    else return (T)*p;
+}
+template <typename T, typename MT>
 __global__ void __launch_bounds__(256) mg_cheb_kernel(long long N, const T* b, const T* y, T* x, T* d,
-                                                      const T* mi, PairPrec<T> pp, const double* coef, int mode,
+                                                      const MT* mi, PairPrec<T> pp, const double* coef, int mode,
                                                       const int* skip, FaultK<T> fk)
 {
     if (skip && *skip) return;
@@ -260,7 +270,13 @@ __global__ void __launch_bounds__(256) mg_cheb_kernel(long long N, const T* b, c
         T r[3], z[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) r[c] = b[c * N + n] - (y ? y[c * N + n] : T(0));
-        Prec<T, 0>::apply(mi, N, n, r, z);
+        {
+            const T i0 = mg_ld<T>(mi + n), i1 = mg_ld<T>(mi + N + n), i2 = mg_ld<T>(mi + 2 * N + n);
+            const T i3 = mg_ld<T>(mi + 3 * N + n), i4 = mg_ld<T>(mi + 4 * N + n), i5 = mg_ld<T>(mi + 5 * N + n);
+            z[0] = i0 * r[0] + i1 * r[1] + i2 * r[2];
+            z[1] = i1 * r[0] + i3 * r[1] + i4 * r[2];
+            z[2] = i2 * r[0] + i4 * r[1] + i5 * r[2];
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const long long k = c * N + n;
@@ -327,11 +343,17 @@ PairPrec<T> level_pairs(gm_ctx* x)
     return pp;
 }
 
+// storage type of the smoother's nodal block inverses
 template <typename T>
-const T* level_inv(gm_ctx* x)
+struct MinvType { using type = T; };
+template <>
+struct MinvType<float> { using type = __nv_bfloat16; };
+
+template <typename T>
+const typename MinvType<T>::type* level_inv(gm_ctx* x)
 {
     if constexpr (sizeof(T) == 8) return x->dKinv64.as<T>();
-    else return x->dKinv32.as<T>();
+    else return x->dKinv16.as<__nv_bfloat16>();
 }
 
 // the level's vectors in the solve precision
@@ -546,7 +568,7 @@ int estimate_lmax(gm_ctx* c, MGLevel& L)
         if ((rc = apply_kt(x, v, L.y, nullptr, 0))) return rc;
         FaultK<float> nofk = level_fault<float>(x);
         nofk.D = nullptr;
-        mg_cheb_kernel<float><<<GM_RED_BLOCKS, 256>>>(x->N, L.y, nullptr, L.x, L.d, x->dKinv32.as<float>(),
+        mg_cheb_kernel<float><<<GM_RED_BLOCKS, 256>>>(x->N, L.y, nullptr, L.x, L.d, level_inv<float>(x),
                                                       level_pairs<float>(x), unit, CHEB_XZERO | CHEB_NO_D, nullptr,
                                                       nofk);
         GM_LAUNCHED(c);
