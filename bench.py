@@ -409,7 +409,9 @@ def run_gm(args, rank, world, local_rank):
             "config": dict(cfg, dofs=ndof, newton_rtol=NEWTON_RTOL, inner_rtol=INNER_RTOL, outer_rtol=OUTER_RTOL,
                            steps_timed=f"{W}..{W + K - 1} of the schedule",
                            l2="flushed (512 MB write) between timed steps and between timed applies",
-                           inner_solvers="K_T: PCG with a geometric multigrid V-cycle; A22: Jacobi PCG; "
+                           inner_solvers="K_T: PCG with a geometric multigrid V-cycle (degree-2 Chebyshev "
+                                         "smoothing with nodal / lip-pair block Jacobi, coarsest grid of at least "
+                                         "10 cells per direction with a degree-24 polynomial); A22: Jacobi PCG; "
                                          "the FP64 comparison uses the same preconditioners in FP64",
                            parallelism=f"replicas{world}" if world > 1 else "single"),
             "roofline": roof, "apply": apply, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e, "tet": tet,
