@@ -727,11 +727,20 @@ extern "C" int gm_get_state(gm_ctx* c, double* u, double* p, double* slip, doubl
     GM_CUDA_TRY(c, cudaSetDevice(c->device));
     GM_CUDA_TRY(c, cudaDeviceSynchronize());
     const long long N = c->N, P = c->P, nb = c->g.nb;
-    std::vector<double> uh;
-    if (u || slip) {
-        uh.resize(3 * N);
-        GM_CUDA_TRY(c, cudaMemcpy(uh.data(), c->du_n.p, 3 * N * 8, cudaMemcpyDeviceToHost));
-        if (u) std::copy(uh.begin(), uh.end(), u);
+    // u straight into the caller's array; the slip needs only the two lip planes
+    std::vector<double> lips;
+    const double* ul = nullptr;     // lip planes: (component, lip, pair)
+    if (u) GM_CUDA_TRY(c, cudaMemcpy(u, c->du_n.p, 3 * N * 8, cudaMemcpyDeviceToHost));
+    if (slip && c->has_fault) {
+        lips.resize(6 * nb);
+        for (int d = 0; d < 3; ++d)
+            for (int s = 0; s < 2; ++s) {
+                const long long off = d * N + nb * (c->g.kf + s);
+                if (u) std::copy(u + off, u + off + nb, lips.begin() + (2 * d + s) * nb);
+                else GM_CUDA_TRY(c, cudaMemcpy(lips.data() + (2 * d + s) * nb, c->du_n.as<double>() + off, nb * 8,
+                                               cudaMemcpyDeviceToHost));
+            }
+        ul = lips.data();
     }
     if (p) {
         GM_CUDA_TRY(c, cudaMemcpy(p, c->dp_n.p, N * 8, cudaMemcpyDeviceToHost));
@@ -741,8 +750,7 @@ extern "C" int gm_get_state(gm_ctx* c, double* u, double* p, double* slip, doubl
     if (slip && c->has_fault) {
         for (long long q = 0; q < P; ++q) {
             double j[3];
-            for (int d = 0; d < 3; ++d)
-                j[d] = uh[d * N + q + nb * (c->g.kf + 1)] - uh[d * N + q + nb * c->g.kf];
+            for (int d = 0; d < 3; ++d) j[d] = ul[(2 * d + 1) * nb + q] - ul[(2 * d) * nb + q];
             slip[q] = c->t1[0] * j[0] + c->t1[1] * j[1] + c->t1[2] * j[2];
             slip[P + q] = c->t2[0] * j[0] + c->t2[1] * j[1] + c->t2[2] * j[2];
         }
@@ -761,13 +769,14 @@ extern "C" int gm_set_state(gm_ctx* c, const double* u, const double* p, const d
     const long long N = c->N, P = c->P;
     if (u) GM_CUDA_TRY(c, cudaMemcpy(c->du_n.p, u, 3 * N * 8, cudaMemcpyHostToDevice));
     if (p) {
-        std::vector<double> ph(p, p + N);
+        GM_CUDA_TRY(c, cudaMemcpy(c->dp_n.p, p, N * 8, cudaMemcpyHostToDevice));
+        // a tied upper lip carries no unknown: its slot is 0 on the device
         if (c->has_fault && c->g.tied)
-            for (long long q = 0; q < c->g.nb; ++q) ph[q + c->g.nb * (c->g.kf + 1)] = 0.0;
-        GM_CUDA_TRY(c, cudaMemcpy(c->dp_n.p, ph.data(), N * 8, cudaMemcpyHostToDevice));
+            GM_CUDA_TRY(c, cudaMemset(c->dp_n.as<double>() + c->g.nb * (c->g.kf + 1), 0, c->g.nb * 8));
     }
     if (dlie && c->has_fault) GM_CUDA_TRY(c, cudaMemcpy(c->ddlie_n.p, dlie, 2 * P * 8, cudaMemcpyHostToDevice));
     if (flags && c->has_fault) GM_CUDA_TRY(c, cudaMemcpy(c->dflags_n.p, flags, P, cudaMemcpyHostToDevice));
+    GM_CUDA_TRY(c, cudaDeviceSynchronize());
     return GM_OK;
 }
 

@@ -2,8 +2,8 @@
 // inner solves of Prevost's partitioned CG, Sec. 3.3.2).  Every scalar of the
 // recurrence (r.z, p.q, alpha, beta, the stopping test) stays on the device:
 // each reduction ends in the last block of its kernel, which sums the
-// per-block partials in block order (deterministic) and updates the solve's
-// state.  The host launches iterations in chunks and reads the state once per
+// per-block partials in a fixed assignment and tree (deterministic) and
+// updates the solve's state.  The host launches iterations in chunks and reads the state once per
 // chunk; once the state says done, every later kernel of the chunk (the
 // operator's included, through the skip flag) returns at once.
 //
