@@ -243,10 +243,13 @@ int gm_set_friction(gm_ctx* ctx, const double* f_host, int64_t n);
 /* Preconditioner of the K_T inner solves, FP32 and FP64 (the paper leaves the
  * inner solvers open, Sec. 3.3.2).  kind 0: block Jacobi, 3x3 nodal blocks and
  * 6x6 blocks for the two lips of each fault pair.  kind 1 (default): one
- * geometric multigrid V-cycle (grids halved within each fault block,
- * Chebyshev-smoothed with that block Jacobi), built on first use (its set-up
- * synchronises); grids whose cell counts or fault index cannot be halved keep
- * kind 0.  The converged solutions agree to the solver tolerances.  GM_EINVAL
+ * geometric multigrid V-cycle (grids halved within each fault block down to
+ * about 10 cells per direction, degree-2 Chebyshev smoothing with that block
+ * Jacobi, a degree-24 Chebyshev polynomial on the coarsest grid), built on
+ * first use (its set-up synchronises); grids whose cell counts or fault index
+ * cannot be halved keep kind 0.  The environment variables GM_MG_MIN_CELLS,
+ * GM_MG_SMOOTH_DEG, GM_MG_COARSE_DEG, GM_MG_SMOOTH_LO and GM_MG_COARSE_LO,
+ * read at set-up, override these choices (tuning only).  The converged solutions agree to the solver tolerances.  GM_EINVAL
  * for another kind. */
 int gm_set_preconditioner(gm_ctx* ctx, int kind);
 
